@@ -1,0 +1,266 @@
+"""Benchmark of the surrogate ILU(0) smoother on GB300.
+
+Workload (one step = one smoother sweep = residual + forward + backward over
+the whole interior): one macro-tetrahedron at level 7 (333,375 interior
+points), reference tetrahedron with every coordinate moved by U(-0.1, 0.1)
+(seed 3), kappa = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), surrogate degree
+6, MIXED precision (FP32 substitutions and surrogate evaluation, FP64 residual
+and update), b ~ U(-1, 1) (seed 4), x0 = 0.  Inputs are smaller than L2, so a
+256 MiB buffer is written between timed steps (L2 flush).
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+LEVEL, DEG, TET_SEED, RHS_SEED = 7, 6, 3, 4
+COEFF = ("sinprod", 1.0, 0.5, 0)
+METRIC = "smoother DoF-sweeps/s (MIXED: FP32 sweeps, FP64 residual/update)"
+UNIT = "DoF-sweeps/s"
+WORKLOAD = "surrogate ILU(0) smoother sweep, single macro-tet L7 (333375 interior DoF), kappa=1+0.5sin sin sin, deg 6"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def interior(level):
+    n = 2 ** level
+    return (n - 1) * (n - 2) * (n - 3) // 6
+
+
+def rows(level):
+    n = 2 ** level
+    return (n - 3) * (n - 2) // 2
+
+
+def algorithmic(level, deg):
+    """Per-launch algorithmic bytes / FLOPs of the three kernels (MIXED,
+    variable coefficient): each vector element moved once, tables once."""
+    nint, nr = interior(level), rows(level)
+    return {
+        # x, b, kappa read (8 B each), r written (4 B)
+        "residual": {"bytes": nint * 28, "flops": nint * 242},
+        # r read, w written (4 B each) + forward table (7 functions x (deg+1) floats per row)
+        "forward": {"bytes": nint * 8 + nr * 7 * (deg + 1) * 4, "flops": nint * (14 * deg + 14)},
+        # w read, x read + written, backward table (8 functions)
+        "backward": {"bytes": nint * 20 + nr * 8 * (deg + 1) * 4, "flops": nint * (16 * deg + 17)},
+    }
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def cpu_oracle_sample(steps=8):
+    """The oracle, as it stands, on the same workload: set-up (untimed), then
+    `steps` matrix-free sweeps, each = evaluate the surrogates at every
+    interior point + one Alg. 2 sweep.  Single-threaded."""
+    from oracle import oracle as O
+    N = 2 ** LEVEL
+    P = si.macro_tet(TET_SEED)
+    pr = O.Problem(P, LEVEL, O.Coeff(*COEFF), deg=DEG)
+    b = si.rhs(LEVEL, RHS_SEED)
+    x = np.zeros(O.num_nodes(N))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Ls, Dinv = O.eval_surrogates(N, pr.deg, pr.coefs)
+        O.smooth(pr.A, N, Ls, Dinv, x, b, 1)
+    dt = time.perf_counter() - t0
+    return {"value": interior(LEVEL) * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"L7 workload, {steps} sweeps, each re-evaluating the eight surrogates at all "
+                      f"{interior(LEVEL)} interior points (FP64, 1 thread), {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps = max(1, min(args.steps, 8))
+    cb = cpu_oracle_sample(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": 0, "ms_per_step": 1e3 * interior(LEVEL) / cb["value"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "level": LEVEL, "degree": DEG,
+                                            "precision": "F64 (oracle)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_2210_15280_gb300 as g
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    W = max(3, args.warmup)
+    K = max(1, args.steps)
+
+    P = si.macro_tet(TET_SEED)
+    t = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=g.MIXED, device=local)
+    nn = g.num_nodes(LEVEL)
+    b_h = si.rhs(LEVEL, RHS_SEED)
+    b = torch.tensor(b_h, dtype=torch.float64, device="cuda")
+    x = torch.zeros(nn, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(W):
+        t.smooth(x, b, 1)
+    torch.cuda.synchronize()
+    t.profile(True)
+    t.profile_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        t.smooth(x, b, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_steps = [a.elapsed_time(bb) for a, bb in ev]
+    total_ms = sum(ms_steps)
+    kms, launches = t.profile_read()
+    t.profile(False)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * interior(LEVEL) * K / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    xh = np.zeros(nn)
+    t.smooth_host(xh, b_h, 1)
+    E = max(3, min(K, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        t.smooth_host(xh, b_h, 1)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * interior(LEVEL) * E / e2e_s
+
+    # roofline of the dominant kernel
+    alg = algorithmic(LEVEL, DEG)
+    names = ["residual", "forward", "backward"]
+    per_launch = {nm: kms[i] / K for i, nm in enumerate(names)}
+    dom = max(names, key=lambda nm: per_launch[nm])
+    hbm, src = peaks()
+    if dom == "residual":
+        achieved = alg[dom]["flops"] / (per_launch[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "residual_kernel (FP64)",
+                "peak_source": "FP64 unit counts x max clock"}
+    else:
+        achieved = alg[dom]["bytes"] / (per_launch[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": f"{dom}_kernel", "peak_source": src}
+    roof["kernel_ms_per_launch"] = {nm: round(v, 5) for nm, v in per_launch.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "level": LEVEL, "degree": DEG, "precision": "MIXED",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nn * 8,
+                    "d2h_bytes_per_step": nn * 8},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(8)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

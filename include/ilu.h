@@ -1,0 +1,255 @@
+/*
+ * ilu.h -- C ABI of the GB300 matrix-free surrogate ILU(0) smoother.
+ *
+ * The operation is the smoother of Drzisga, Wagner and Wohlmuth, "A
+ * matrix-free ILU realization based on surrogates" (arXiv 2210.15280):
+ *
+ *     x <- x + R_t^T (L~ D~ L~^T)^{-1} R_t (b - A x)          (Sec. 2.1, Alg. 2)
+ *
+ * on the interior points of one uniformly refined macro-tetrahedron t, where
+ * A is the P1 stiffness matrix of -div(kappa grad u) (Sec. 2.1), L~ and D~ are
+ * surrogate polynomials fitted to the exact ILU(0) factors of the interior
+ * block (Sec. 3, Sec. 4.1, Alg. 1), evaluated on the fly in the sweep, and the
+ * V2 boundary rule of Alg. 2 is used (L~^p_d = 0 where p+d is not interior).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  level L in [2, 10], N = 2^L.  Logical grid G = {(x,y,z) in Z^3 :
+ *   x,y,z >= 0, x+y+z <= N}, interior {x,y,z >= 1, x+y+z <= N-1} (Sec. 2.1).
+ * Vectors.  Full-grid, lexicographic (z slowest, then y, then x; Sec. 2.1),
+ *   length ilu_num_nodes(L) = (N+1)(N+2)(N+3)/6.  x entries on the boundary are
+ *   Dirichlet data: read, never written.  b entries on the boundary are ignored.
+ *   Element type: double for ILU_F64 and ILU_MIXED, float for ILU_F32.
+ *   Device pointers unless the entry point says "host".  Vectors are owned by
+ *   the caller; the handle owns its coefficients, tables and scratch.
+ * Macro-tetrahedron.  12 doubles: vertices p1..p4 (x,y,z each).  The logical
+ *   point (x,y,z) sits at p1 + ((p2-p1) x + (p3-p1) y + (p4-p1) z) / N.
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous on it unless a host output is requested.
+ * Errors.  Every entry point returns an ilu_status; no exception crosses the
+ *   ABI.  ilu_last_error() gives a thread-local message for the last failure.
+ *   ILU_ECUDA and ILU_ETIMEOUT leave the handle unusable: destroy it.
+ */
+#ifndef ILU_H
+#define ILU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ILU_OK = 0,
+  ILU_EINVAL = 1,     /* bad argument: level, degree, degenerate tet, null pointer, ... */
+  ILU_ENOMEM = 2,     /* host or device allocation failed, or a memory budget is exceeded */
+  ILU_ECUDA = 3,      /* a CUDA call failed; the handle is unusable */
+  ILU_ESINGULAR = 4,  /* setup met a non-positive pivot or a non-positive surrogate 1/D */
+  ILU_ENOTCONV = 5,   /* an iterative solve stopped at max_iter */
+  ILU_ETIMEOUT = 6,   /* a bounded device wait ran out; the handle is unusable */
+  ILU_EBUSY = 7,      /* the request loop is full or shutting down */
+  ILU_ENODEV = 8      /* no CUDA device, or the handle has no device part */
+} ilu_status;
+
+typedef enum { ILU_F64 = 0, ILU_F32 = 1, ILU_MIXED = 2 } ilu_precision;
+
+typedef enum {
+  ILU_COEFF_CONST = 0,   /* kappa = c0 */
+  ILU_COEFF_SINPROD = 1, /* kappa = c0 + amp sin(2 pi x) sin(2 pi y) sin(2 pi z) */
+  ILU_COEFF_KAPPA_I = 2  /* kappa = 1 + 10 (x^i + y^i + z^i)  (Sec. 4.2) */
+} ilu_coeff_kind;
+
+/* Scalar diffusion coefficient kappa(x) of Sec. 2.1, evaluated at physical
+ * points.  Element values are the mean of the four vertex values. */
+typedef struct {
+  int kind;   /* ilu_coeff_kind */
+  double c0;  /* CONST / SINPROD offset */
+  double amp; /* SINPROD amplitude */
+  int ipow;   /* KAPPA_I exponent i */
+} ilu_coeff;
+
+/* Options.  Zero-initialise, then call ilu_opts_default. */
+typedef struct {
+  int deg[3];          /* surrogate degrees dg_x, dg_y, dg_z (Sec. 4.1); <0: use poly_degree */
+  int sample_level;    /* coarse sampling level L_H (Sec. 4.1); <0: min(L, 5) */
+  double ridge;        /* relative Tikhonov weight of the fit; <0: 1e-6 */
+  int precision;       /* ilu_precision */
+  int slabs;           /* z-slabs (CTAs) per tet in the sweep; <=0: automatic */
+  int device;          /* CUDA device ordinal; -1: host-only handle (setup only) */
+  long long max_wait_spins; /* bound on device-side spin waits; <=0: default */
+} ilu_opts;
+
+typedef struct ilu_tet_s *ilu_tet;
+typedef struct ilu_batch_s *ilu_batch;
+typedef struct ilu_server_s *ilu_server;
+
+/* ---------------------------------------------------------------- setup -- */
+
+/* Fill opts with defaults (deg -1, sample_level -1, ridge 1e-6, ILU_MIXED,
+ * automatic slabs, device 0).  Returns ILU_EINVAL on NULL. */
+ilu_status ilu_opts_default(ilu_opts *opts);
+
+/* Set up the smoother for one macro-tetrahedron (Sec. 4.1, Alg. 1): assemble
+ * the interior-restricted stencils, run the streaming LDL^T factorisation in
+ * FP64 on the host, fit the eight surrogates (L_d for d in D_l, and 1/D_c) by
+ * ridge-regularised least squares on the sample sets S_d, build the per-row
+ * evaluation tables and upload them to `opts->device`.
+ *   macro_tet   12 doubles (host), see conventions; must be non-degenerate.
+ *   level       2..10.
+ *   coeff       kappa (host); NULL means kappa = 1.
+ *   poly_degree isotropic surrogate degree 0..10, used where opts->deg < 0.
+ *   opts        NULL for defaults.
+ *   out         receives the handle (NULL on failure).
+ * Errors: ILU_EINVAL, ILU_ENOMEM, ILU_ESINGULAR, ILU_ECUDA, ILU_ENODEV. */
+ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coeff, int poly_degree,
+                     const ilu_opts *opts, ilu_tet *out);
+
+/* Release the handle, its device memory and graphs.  NULL is accepted. */
+ilu_status ilu_destroy(ilu_tet t);
+
+/* Replace the fitted surrogate by externally supplied coefficients (same
+ * layout as ilu_export_surrogate) and rebuild the evaluation tables.  Lets a
+ * caller run the sweep with surrogates fitted elsewhere. */
+ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n);
+
+/* Copy the surrogate coefficients to host memory: 8 blocks (w s se bnw bn bc
+ * be, then 1/D) of (dgx+1)(dgy+1)(dgz+1) doubles, coefficient of
+ * P_i(2hx-1) P_j(2hy-1) P_k(2hz-1) at index (i*(dgy+1)+j)*(dgz+1)+k, P_n the
+ * Legendre polynomials and h = 2^-L.  n must be >= the block total. */
+ilu_status ilu_export_surrogate(ilu_tet t, double *coefs, size_t n);
+
+/* Number of doubles ilu_export_surrogate writes. */
+size_t ilu_surrogate_size(ilu_tet t);
+
+/* Host FP64 value of the surrogates at interior point (x,y,z), computed from
+ * the same per-row tables the device uses: out[0..6] = L~^p_d for d in D_l
+ * (V2-masked), out[7] = 1/D~^p.  Host only. */
+ilu_status ilu_eval_surrogate(ilu_tet t, int x, int y, int z, double out[8]);
+
+/* Host FP64 exact factor entries of Alg. 1 at interior point (x,y,z), kept
+ * only when the handle was created at level <= 7: out[0..6] = L^p_d, out[7] =
+ * D^p_c.  Returns ILU_EINVAL if not kept. */
+ilu_status ilu_exact_factor(ilu_tet t, int x, int y, int z, double out[8]);
+
+/* Host FP64 stencil A^p_d of the full operator at grid point (x,y,z) (all 15
+ * directions in the order w s se bnw bn bc be c e n nw tse ts tc tw). */
+ilu_status ilu_stencil(ilu_tet t, int x, int y, int z, double out[15]);
+
+/* ------------------------------------------------------------- smoothing -- */
+
+/* `sweeps` applications of the smoother (Alg. 2) to device vectors x (in/out)
+ * and b.  Each sweep: r = b - A x on the interior (FP64 in ILU_F64/MIXED,
+ * FP32 in ILU_F32), forward substitution with L~, scaling by D~^-1 and
+ * backward substitution with L~^T in the handle's precision, x += w.
+ * res_norms (host, nullable, length sweeps) receives ||b - A x||_2 over the
+ * interior before each sweep; giving it makes the call synchronous. */
+ilu_status ilu_smooth(ilu_tet t, void *x, const void *b, int sweeps, void *stream, double *res_norms);
+
+/* Same as ilu_smooth on HOST vectors: copies x and b to the device, smooths,
+ * copies x back (synchronous). */
+ilu_status ilu_smooth_host(ilu_tet t, void *x_host, const void *b_host, int sweeps, double *res_norms);
+
+/* r = b - A x on the interior (boundary entries of r set to 0).  r (device,
+ * nullable) has the handle's vector type; norm2 (host, nullable) receives
+ * ||r||_2 and makes the call synchronous. */
+ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double *norm2, void *stream);
+
+typedef enum { ILU_RICHARDSON = 0, ILU_PCG = 1 } ilu_method;
+
+/* Solve A x = b on the interior (boundary of x = Dirichlet data) to
+ * ||b - A x||_2 <= rtol ||b||_2 (interior norms) with smoothed Richardson
+ * (defect correction, x += C~^-1 r) or CG preconditioned by C~ (Sec. 4.2).
+ * Residuals and updates are FP64 unless the handle is ILU_F32.
+ * iters/rel_res (host, nullable) receive the iteration count and the final
+ * relative residual.  Synchronous.  ILU_ENOTCONV at max_iter. */
+ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
+                     int *iters, double *rel_res);
+
+/* ----------------------------------------------------------------- batch -- */
+
+/* Group tets (same precision, any levels and degrees) for one persistent
+ * launch per sweep.  The batch keeps references to the tets, which must
+ * outlive it. */
+ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, ilu_batch *out);
+ilu_status ilu_batch_destroy(ilu_batch b);
+
+/* One call smooths every tet of the batch `sweeps` times: x[i], b[i] are
+ * device vectors of tet i.  The sweep kernels are launched once per pass for
+ * the whole batch (captured in a CUDA graph after the first call). */
+ilu_status ilu_batch_smooth(ilu_batch bt, void *const *x, const void *const *b, int sweeps, void *stream);
+
+/* ----------------------------------------------------------- request loop -- */
+
+typedef struct {
+  double hbm_budget_bytes; /* device bytes the loop may hold for requests; <=0: 80% of free */
+  int max_slots;           /* requests on the device at once; <=0: 64 */
+  int device;
+  int precision;           /* ilu_precision for admitted work */
+} ilu_server_opts;
+
+typedef struct {
+  double macro_tet[12];
+  int level;
+  ilu_coeff coeff;
+  int poly_degree;
+  int method;        /* ilu_method */
+  double rtol;
+  int max_iter;
+  const double *b;   /* host, full grid, ilu_num_nodes(level) doubles; copied on submit */
+  const double *x0;  /* host, nullable (zeros): start vector and Dirichlet data */
+} ilu_request;
+
+typedef struct {
+  ilu_status status;
+  int iters;
+  double rel_res;
+  double latency_ms;  /* submit to completion */
+  double *x;          /* host solution, owned by the server until ilu_server_release */
+  size_t n;
+} ilu_result;
+
+typedef struct {
+  long long submitted, completed, failed;
+  double p50_ms, p99_ms, solves_per_s;
+  int max_concurrent;
+} ilu_stats;
+
+ilu_status ilu_server_create(const ilu_server_opts *opts, ilu_server *out);
+/* Queue a request; returns at once with a ticket.  ILU_EBUSY if shutting down. */
+ilu_status ilu_server_submit(ilu_server s, const ilu_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (<0: forever) for a ticket.  ILU_ETIMEOUT if not done. */
+ilu_status ilu_server_wait(ilu_server s, uint64_t ticket, int timeout_ms, ilu_result *res);
+/* Free the host solution of a finished ticket. */
+ilu_status ilu_server_release(ilu_server s, uint64_t ticket);
+ilu_status ilu_server_stats(ilu_server s, ilu_stats *st);
+ilu_status ilu_server_destroy(ilu_server s);
+
+/* --------------------------------------------------------------- tracing -- */
+
+/* Per-kernel device timing of one handle.  With enable != 0 every kernel the
+ * handle launches is bracketed by CUDA events on its stream; ilu_profile_read
+ * synchronises, returns the accumulated milliseconds of the residual, forward
+ * and backward kernels in ms[0..2], their launch count in *launches, and
+ * clears the counters.  The paper has no counterpart (it profiles with
+ * LIKWID); this is the library's own tracing. */
+ilu_status ilu_profile_enable(ilu_tet t, int enable);
+ilu_status ilu_profile_read(ilu_tet t, double ms[3], long long *launches);
+
+/* ------------------------------------------------------------- utilities -- */
+
+/* (N+1)(N+2)(N+3)/6 for N = 2^level; 0 for level out of [2, 10]. */
+size_t ilu_num_nodes(int level);
+/* (N-1)(N-2)(N-3)/6; 0 for level out of range. */
+size_t ilu_num_interior(int level);
+/* Lexicographic index of (x,y,z), or -1 if the point is not in G. */
+long long ilu_index(int level, int x, int y, int z);
+/* Thread-local message of the last failed call on this thread. */
+const char *ilu_last_error(void);
+/* Library version string. */
+const char *ilu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ILU_H */

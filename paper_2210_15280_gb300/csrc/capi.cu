@@ -1,0 +1,517 @@
+// capi.cu -- the extern "C" entry points declared in include/ilu.h.
+//
+// A handle (ilu_tet) owns the FP64 host set-up (setup.cpp) and its device
+// part: the per-row surrogate tables in the sweep precision, kappa at the grid
+// points for a variable coefficient, one full-grid scratch vector w (the
+// residual, then the substitution result, in place), the slab progress flags
+// and a status word that bounded device waits write on timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ilu.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+using namespace ilu;
+
+namespace {
+
+thread_local std::string g_err;
+
+ilu_status fail(ilu_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+ilu_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(ILU_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr long long kDefaultSpins = 4000000;  // ~a few seconds of polling with nanosleep
+
+}  // namespace
+
+struct ilu_tet_s {
+  HostTet host;
+  int precision = ILU_MIXED;
+  int device = -1;
+  long long max_spins = kDefaultSpins;
+  bool failed = false;
+  DevTet dev = {};
+  int slab_layers = 16, nslabs = 1;
+  void *d_tabF = nullptr, *d_tabB = nullptr, *d_w = nullptr;
+  double *d_kappa = nullptr, *d_partials = nullptr, *d_norms = nullptr;
+  int *d_flags = nullptr;
+  LaunchStatus *d_status = nullptr, *h_status = nullptr;
+  int nblocks = 0, norms_cap = 0;
+  void *d_xs = nullptr, *d_bs = nullptr;  // staging for ilu_smooth_host
+  // tracing: CUDA event pairs around each kernel launch
+  bool prof = false;
+  struct Ev {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> ev_used;
+  std::vector<cudaEvent_t> ev_pool;
+  long long launches = 0;
+  std::mutex mu;
+  size_t elem() const { return precision == ILU_F32 ? sizeof(float) : sizeof(double); }
+  int kind() const { return precision == ILU_F64 ? kSweepF64 : (precision == ILU_F32 ? kSweepF32 : kSweepMixed); }
+  size_t nnodes() const { return (size_t)grid_nodes(host.N); }
+};
+
+namespace {
+
+void free_device(ilu_tet t) {
+  if (t->device < 0) return;
+  cudaSetDevice(t->device);
+  for (auto &e : t->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : t->ev_pool) cudaEventDestroy(e);
+  t->ev_used.clear();
+  t->ev_pool.clear();
+  cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa);
+  cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
+  cudaFree(t->d_xs); cudaFree(t->d_bs);
+  if (t->h_status) cudaFreeHost(t->h_status);
+  t->d_tabF = t->d_tabB = t->d_w = nullptr;
+  t->d_kappa = t->d_partials = t->d_norms = nullptr;
+  t->d_flags = nullptr; t->d_status = nullptr; t->h_status = nullptr; t->d_xs = t->d_bs = nullptr;
+}
+
+// choose z-slabs: one warp per face layer, at most 32 warps per CTA, the
+// shared-memory ring (4 levels x layers x (N/2+2) values) within ~200 KB
+void choose_slabs(ilu_tet t, int requested) {
+  const int N = t->host.N;
+  const int layers = std::max(1, N - 3);
+  const size_t e = t->elem();
+  int zb = 16;
+  if (requested > 0) zb = (layers + requested - 1) / requested;
+  zb = std::max(1, std::min(zb, 32));
+  while (zb > 1 && (size_t)4 * zb * (N / 2 + 2) * e > 200 * 1024) zb /= 2;
+  zb = std::min(zb, layers);
+  t->slab_layers = zb;
+  t->nslabs = (layers + zb - 1) / zb;
+}
+
+ilu_status upload(ilu_tet t) {
+  HostTet &h = t->host;
+  CK(cudaSetDevice(t->device), "cudaSetDevice");
+  const size_t nn = t->nnodes();
+  const bool f64 = t->precision == ILU_F64;
+  const size_t nf = h.tabF64.size(), nb = h.tabB64.size();
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  CK(cudaMalloc(&t->d_tabF, std::max<size_t>(nf, 1) * es), "cudaMalloc tables");
+  CK(cudaMalloc(&t->d_tabB, std::max<size_t>(nb, 1) * es), "cudaMalloc tables");
+  if (nf) CK(cudaMemcpy(t->d_tabF, f64 ? (const void *)h.tabF64.data() : (const void *)h.tabF32.data(), nf * es,
+                        cudaMemcpyHostToDevice), "upload tables");
+  if (nb) CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(), nb * es,
+                        cudaMemcpyHostToDevice), "upload tables");
+  if (!h.const_kappa) {
+    CK(cudaMalloc(&t->d_kappa, nn * sizeof(double)), "cudaMalloc kappa");
+    CK(cudaMemcpy(t->d_kappa, h.kappa.data(), nn * sizeof(double), cudaMemcpyHostToDevice), "upload kappa");
+  }
+  CK(cudaMalloc(&t->d_w, nn * t->elem()), "cudaMalloc scratch");
+  CK(cudaMemset(t->d_w, 0, nn * t->elem()), "cudaMemset scratch");
+  CK(cudaMalloc(&t->d_flags, sizeof(int) * (2 * t->nslabs + 2)), "cudaMalloc flags");
+  CK(cudaMemset(t->d_flags, 0, sizeof(int) * (2 * t->nslabs + 2)), "cudaMemset flags");
+  CK(cudaMalloc(&t->d_status, sizeof(LaunchStatus)), "cudaMalloc status");
+  CK(cudaMemset(t->d_status, 0, sizeof(LaunchStatus)), "cudaMemset status");
+  CK(cudaMallocHost(&t->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
+  std::memset(t->h_status, 0, sizeof(LaunchStatus));
+  t->nblocks = std::max(1, residual_blocks(h.N));
+  CK(cudaMalloc(&t->d_partials, sizeof(double) * t->nblocks), "cudaMalloc partials");
+  t->norms_cap = 0;
+  DevTet &d = t->dev;
+  d.L = h.L; d.N = h.N; d.h = h.h; d.dx = h.dx; d.rstride = h.rstride;
+  d.nslabs = t->nslabs; d.slab_layers = t->slab_layers;
+  d.const_kappa = h.const_kappa ? 1 : 0;
+  d.tabF = t->d_tabF; d.tabB = t->d_tabB; d.kappa = t->d_kappa; d.w = t->d_w; d.flags = t->d_flags;
+  std::memcpy(d.A15, h.A15, sizeof(d.A15));
+  std::memcpy(d.Wstar, h.Wstar, sizeof(d.Wstar));
+  return ILU_OK;
+}
+
+ilu_status upload_tables(ilu_tet t) {
+  HostTet &h = t->host;
+  CK(cudaSetDevice(t->device), "cudaSetDevice");
+  const bool f64 = t->precision == ILU_F64;
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  if (h.tabF64.size())
+    CK(cudaMemcpy(t->d_tabF, f64 ? (const void *)h.tabF64.data() : (const void *)h.tabF32.data(),
+                  h.tabF64.size() * es, cudaMemcpyHostToDevice), "upload tables");
+  if (h.tabB64.size())
+    CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(),
+                  h.tabB64.size() * es, cudaMemcpyHostToDevice), "upload tables");
+  return ILU_OK;
+}
+
+// the surrogate pivot inverse must be positive everywhere for L~ D~ L~^T to
+// be symmetric positive definite
+ilu_status check_surrogate(const HostTet &h) {
+  const int N = h.N;
+  for (int z = 1; z <= N - 3; ++z)
+    for (int y = 1; y <= N - 2 - z; ++y)
+      for (int x = 1; x <= N - 1 - y - z; ++x) {
+        double v[8];
+        host_eval_tables(h, x, y, z, v);
+        if (!(v[7] > 0.0) || !std::isfinite(v[7]))
+          return fail(ILU_ESINGULAR, "surrogate 1/D is not positive at an interior point");
+      }
+  return ILU_OK;
+}
+
+ilu_status ensure_norms(ilu_tet t, int n) {
+  if (t->norms_cap >= n) return ILU_OK;
+  cudaFree(t->d_norms);
+  t->d_norms = nullptr;
+  int cap = std::max(n, 64);
+  CK(cudaMalloc(&t->d_norms, sizeof(double) * cap), "cudaMalloc norms");
+  t->norms_cap = cap;
+  return ILU_OK;
+}
+
+ilu_status check_usable(ilu_tet t) {
+  if (!t) return fail(ILU_EINVAL, "null handle");
+  if (t->device < 0) return fail(ILU_ENODEV, "host-only handle has no device part");
+  if (t->failed) return fail(ILU_ECUDA, "handle failed earlier; destroy it");
+  return ILU_OK;
+}
+
+ilu_status read_status(ilu_tet t, cudaStream_t st) {
+  CK(cudaMemcpyAsync(t->h_status, t->d_status, sizeof(LaunchStatus), cudaMemcpyDeviceToHost, st), "status copy");
+  CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (t->h_status->code != 0) {
+    t->failed = true;
+    return fail(ILU_ETIMEOUT, "a bounded device wait ran out (slab " + std::to_string(t->h_status->where) +
+                                  ", level " + std::to_string(t->h_status->level) + ")");
+  }
+  return ILU_OK;
+}
+
+cudaEvent_t pool_event(ilu_tet t) {
+  if (!t->ev_pool.empty()) {
+    cudaEvent_t e = t->ev_pool.back();
+    t->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// bracket one launch with events when tracing is on
+struct Traced {
+  ilu_tet t;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  Traced(ilu_tet t_, int k, cudaStream_t s) : t(t_), kind(k), st(s) {
+    t->launches++;
+    if (t->prof) {
+      a = pool_event(t);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~Traced() {
+    if (a) {
+      cudaEvent_t b = pool_event(t);
+      cudaEventRecord(b, st);
+      t->ev_used.push_back({kind, a, b});
+    }
+  }
+};
+
+// one sweep on device vectors: residual into w, forward, backward with x += w
+ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStream_t st) {
+  const int P = t->nslabs;
+  CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * (2 * P + 2), st), "reset flags");
+  int used = 0;
+  {
+    Traced tr(t, 0, st);
+    CK(launch_residual(t->dev, t->kind(), x, b, t->d_w, t->d_partials, t->nblocks, &used, st), "residual launch");
+  }
+  if (d_norm_out) {
+    t->launches++;
+    CK(launch_norm_finish(t->d_partials, used, d_norm_out, st), "norm launch");
+  }
+  {
+    Traced tr(t, 1, st);
+    CK(launch_forward(t->dev, t->kind(), t->d_status, t->max_spins, st), "forward launch");
+  }
+  {
+    Traced tr(t, 2, st);
+    CK(launch_backward(t->dev, t->kind(), x, t->d_status, t->max_spins, st), "backward launch");
+  }
+  return ILU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ilu_status ilu_opts_default(ilu_opts *o) {
+  if (!o) return fail(ILU_EINVAL, "null opts");
+  o->deg[0] = o->deg[1] = o->deg[2] = -1;
+  o->sample_level = -1;
+  o->ridge = -1.0;
+  o->precision = ILU_MIXED;
+  o->slabs = 0;
+  o->device = 0;
+  o->max_wait_spins = 0;
+  return ILU_OK;
+}
+
+const char *ilu_last_error(void) { return g_err.c_str(); }
+const char *ilu_version(void) { return "gb300-surrogate-ilu 0.1 (sm_103a)"; }
+
+size_t ilu_num_nodes(int level) {
+  if (level < 2 || level > 10) return 0;
+  return (size_t)grid_nodes(1 << level);
+}
+
+size_t ilu_num_interior(int level) {
+  if (level < 2 || level > 10) return 0;
+  return (size_t)grid_interior(1 << level);
+}
+
+long long ilu_index(int level, int x, int y, int z) {
+  if (level < 2 || level > 10) return -1;
+  const int N = 1 << level;
+  if (!in_grid(N, x, y, z)) return -1;
+  return (long long)grid_index(N, x, y, z);
+}
+
+ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coeff, int poly_degree,
+                     const ilu_opts *opts, ilu_tet *out) {
+  if (!out) return fail(ILU_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!macro_tet) return fail(ILU_EINVAL, "null macro_tet");
+  ilu_opts o;
+  ilu_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.precision < 0 || o.precision > 2) return fail(ILU_EINVAL, "unknown precision");
+  int deg[3];
+  for (int c = 0; c < 3; ++c) deg[c] = o.deg[c] >= 0 ? o.deg[c] : poly_degree;
+  ilu_tet t = new (std::nothrow) ilu_tet_s;
+  if (!t) return fail(ILU_ENOMEM, "out of host memory");
+  t->precision = o.precision;
+  t->device = o.device;
+  t->max_spins = o.max_wait_spins > 0 ? o.max_wait_spins : kDefaultSpins;
+  std::string err;
+  ilu_status st;
+  try {
+    st = host_setup(t->host, macro_tet, level, coeff, deg, o.sample_level, o.ridge, err);
+  } catch (const std::bad_alloc &) {
+    st = ILU_ENOMEM;
+    err = "out of host memory during set-up";
+  }
+  if (st != ILU_OK) {
+    delete t;
+    return fail(st, err);
+  }
+  st = check_surrogate(t->host);
+  if (st != ILU_OK) {
+    delete t;
+    return st;
+  }
+  if (t->device >= 0) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= t->device) {
+      cudaGetLastError();
+      delete t;
+      return fail(ILU_ENODEV, "no CUDA device with that ordinal");
+    }
+    choose_slabs(t, o.slabs);
+    st = upload(t);
+    if (st != ILU_OK) {
+      free_device(t);
+      delete t;
+      return st;
+    }
+  }
+  *out = t;
+  return ILU_OK;
+}
+
+ilu_status ilu_destroy(ilu_tet t) {
+  if (!t) return ILU_OK;
+  free_device(t);
+  delete t;
+  return ILU_OK;
+}
+
+size_t ilu_surrogate_size(ilu_tet t) { return t ? t->host.coefs.size() : 0; }
+
+ilu_status ilu_export_surrogate(ilu_tet t, double *coefs, size_t n) {
+  if (!t || !coefs) return fail(ILU_EINVAL, "null argument");
+  if (n < t->host.coefs.size()) return fail(ILU_EINVAL, "output too small");
+  std::memcpy(coefs, t->host.coefs.data(), sizeof(double) * t->host.coefs.size());
+  return ILU_OK;
+}
+
+ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n) {
+  if (!t || !coefs) return fail(ILU_EINVAL, "null argument");
+  if (n != t->host.coefs.size()) return fail(ILU_EINVAL, "coefficient count does not match the handle's degrees");
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(coefs[i])) return fail(ILU_EINVAL, "non-finite coefficient");
+  std::lock_guard<std::mutex> lk(t->mu);
+  std::vector<double> old = t->host.coefs;
+  std::memcpy(t->host.coefs.data(), coefs, sizeof(double) * n);
+  build_row_tables(t->host);
+  ilu_status st = check_surrogate(t->host);
+  if (st != ILU_OK) {
+    t->host.coefs = old;
+    build_row_tables(t->host);
+    return st;
+  }
+  if (t->device >= 0) return upload_tables(t);
+  return ILU_OK;
+}
+
+ilu_status ilu_eval_surrogate(ilu_tet t, int x, int y, int z, double out[8]) {
+  if (!t || !out) return fail(ILU_EINVAL, "null argument");
+  if (!in_interior(t->host.N, x, y, z)) return fail(ILU_EINVAL, "point is not interior");
+  host_eval_tables(t->host, x, y, z, out);
+  return ILU_OK;
+}
+
+ilu_status ilu_exact_factor(ilu_tet t, int x, int y, int z, double out[8]) {
+  if (!t || !out) return fail(ILU_EINVAL, "null argument");
+  const HostTet &h = t->host;
+  if (!h.keep_exact) return fail(ILU_EINVAL, "exact factors are kept only for level <= 7");
+  if (!in_interior(h.N, x, y, z)) return fail(ILU_EINVAL, "point is not interior");
+  // interior lexicographic number of (x,y,z)
+  const int N = h.N;
+  int64_t i = 0;
+  for (int zz = 1; zz < z; ++zz)
+    for (int yy = 1; yy <= N - 2 - zz; ++yy) i += N - 1 - yy - zz;
+  for (int yy = 1; yy < y; ++yy) i += N - 1 - yy - z;
+  i += x - 1;
+  const int64_t nint = grid_interior(N);
+  for (int d = 0; d < 7; ++d) out[d] = h.exactL[(size_t)d * nint + i];
+  out[7] = h.exactD[i];
+  return ILU_OK;
+}
+
+ilu_status ilu_stencil(ilu_tet t, int x, int y, int z, double out[15]) {
+  if (!t || !out) return fail(ILU_EINVAL, "null argument");
+  if (!in_interior(t->host.N, x, y, z)) return fail(ILU_EINVAL, "point is not interior");
+  host_stencil(t->host, x, y, z, out);
+  return ILU_OK;
+}
+
+ilu_status ilu_smooth(ilu_tet t, void *x, const void *b, int sweeps, void *stream, double *res_norms) {
+  ilu_status st = check_usable(t);
+  if (st != ILU_OK) return st;
+  if (!x || !b) return fail(ILU_EINVAL, "null vector");
+  if (sweeps < 0) return fail(ILU_EINVAL, "negative sweep count");
+  if (sweeps == 0) return ILU_OK;
+  std::lock_guard<std::mutex> lk(t->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(t->device), "cudaSetDevice");
+  if (res_norms) {
+    st = ensure_norms(t, sweeps);
+    if (st != ILU_OK) return st;
+  }
+  for (int k = 0; k < sweeps; ++k) {
+    st = sweep(t, x, b, res_norms ? t->d_norms + k : nullptr, s);
+    if (st != ILU_OK) { t->failed = true; return st; }
+  }
+  if (res_norms) {
+    CK(cudaMemcpyAsync(res_norms, t->d_norms, sizeof(double) * sweeps, cudaMemcpyDeviceToHost, s), "norms copy");
+    return read_status(t, s);
+  }
+  return ILU_OK;
+}
+
+ilu_status ilu_smooth_host(ilu_tet t, void *x_host, const void *b_host, int sweeps, double *res_norms) {
+  ilu_status st = check_usable(t);
+  if (st != ILU_OK) return st;
+  if (!x_host || !b_host) return fail(ILU_EINVAL, "null vector");
+  const size_t bytes = t->nnodes() * t->elem();
+  {
+    std::lock_guard<std::mutex> lk(t->mu);
+    CK(cudaSetDevice(t->device), "cudaSetDevice");
+    if (!t->d_xs) CK(cudaMalloc(&t->d_xs, bytes), "cudaMalloc staging");
+    if (!t->d_bs) CK(cudaMalloc(&t->d_bs, bytes), "cudaMalloc staging");
+    CK(cudaMemcpy(t->d_xs, x_host, bytes, cudaMemcpyHostToDevice), "copy x");
+    CK(cudaMemcpy(t->d_bs, b_host, bytes, cudaMemcpyHostToDevice), "copy b");
+  }
+  st = ilu_smooth(t, t->d_xs, t->d_bs, sweeps, nullptr, res_norms);
+  if (st != ILU_OK) return st;
+  std::lock_guard<std::mutex> lk(t->mu);
+  CK(cudaMemcpy(x_host, t->d_xs, bytes, cudaMemcpyDeviceToHost), "copy x back");
+  if (!res_norms) return read_status(t, nullptr);
+  return ILU_OK;
+}
+
+ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double *norm2, void *stream) {
+  ilu_status st = check_usable(t);
+  if (st != ILU_OK) return st;
+  if (!x || !b) return fail(ILU_EINVAL, "null vector");
+  std::lock_guard<std::mutex> lk(t->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(t->device), "cudaSetDevice");
+  // the residual kernel writes interior entries only: clear r's boundary
+  void *dst = r ? r : t->d_w;
+  const int kind = t->precision == ILU_F32 ? kSweepF32 : kSweepF64;
+  if (r) CK(cudaMemsetAsync(r, 0, t->nnodes() * t->elem(), s), "clear r");
+  int used = 0;
+  if (!r && t->precision == ILU_MIXED) {
+    // scratch holds floats in MIXED mode: compute the norm through the mixed kernel
+    CK(launch_residual(t->dev, kSweepMixed, x, b, t->d_w, t->d_partials, t->nblocks, &used, s), "residual launch");
+  } else {
+    CK(launch_residual(t->dev, kind, x, b, dst, t->d_partials, t->nblocks, &used, s), "residual launch");
+  }
+  if (norm2) {
+    st = ensure_norms(t, 1);
+    if (st != ILU_OK) return st;
+    CK(launch_norm_finish(t->d_partials, used, t->d_norms, s), "norm launch");
+    CK(cudaMemcpyAsync(norm2, t->d_norms, sizeof(double), cudaMemcpyDeviceToHost, s), "norm copy");
+    CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
+  return ILU_OK;
+}
+
+ilu_status ilu_profile_enable(ilu_tet t, int enable) {
+  if (!t) return fail(ILU_EINVAL, "null handle");
+  std::lock_guard<std::mutex> lk(t->mu);
+  t->prof = enable != 0;
+  return ILU_OK;
+}
+
+ilu_status ilu_profile_read(ilu_tet t, double ms[3], long long *launches) {
+  if (!t || !ms) return fail(ILU_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(t->mu);
+  ms[0] = ms[1] = ms[2] = 0.0;
+  if (t->device >= 0) {
+    CK(cudaSetDevice(t->device), "cudaSetDevice");
+    for (auto &e : t->ev_used) {
+      CK(cudaEventSynchronize(e.b), "cudaEventSynchronize");
+      float v = 0.f;
+      CK(cudaEventElapsedTime(&v, e.a, e.b), "cudaEventElapsedTime");
+      if (e.kind >= 0 && e.kind < 3) ms[e.kind] += v;
+      t->ev_pool.push_back(e.a);
+      t->ev_pool.push_back(e.b);
+    }
+  }
+  t->ev_used.clear();
+  if (launches) *launches = t->launches;
+  t->launches = 0;
+  return ILU_OK;
+}
+
+}  // extern "C"

@@ -51,13 +51,16 @@ struct ilu_tet_s {
   long long max_spins = kDefaultSpins;
   bool failed = false;
   DevTet dev = {};
-  int slab_layers = 16, nslabs = 1;
+  int nflags = 0;
   void *d_tabF = nullptr, *d_tabB = nullptr, *d_w = nullptr;
   double *d_kappa = nullptr, *d_partials = nullptr, *d_norms = nullptr;
   int *d_flags = nullptr;
   LaunchStatus *d_status = nullptr, *h_status = nullptr;
   int nblocks = 0, norms_cap = 0;
   void *d_xs = nullptr, *d_bs = nullptr;  // staging for ilu_smooth_host
+  void *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_zero = nullptr;  // Krylov vectors
+  double *d_dot = nullptr, *d_scal = nullptr;  // dot partials, scalars
+  double *h_scal = nullptr;                    // pinned copy of the scalars
   // tracing: CUDA event pairs around each kernel launch
   bool prof = false;
   struct Ev {
@@ -85,25 +88,65 @@ void free_device(ilu_tet t) {
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa);
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
   cudaFree(t->d_xs); cudaFree(t->d_bs);
+  cudaFree(t->d_r); cudaFree(t->d_z); cudaFree(t->d_p); cudaFree(t->d_q); cudaFree(t->d_zero);
+  cudaFree(t->d_dot); cudaFree(t->d_scal);
+  if (t->h_scal) cudaFreeHost(t->h_scal);
+  t->d_r = t->d_z = t->d_p = t->d_q = t->d_zero = nullptr;
+  t->d_dot = t->d_scal = t->h_scal = nullptr;
   if (t->h_status) cudaFreeHost(t->h_status);
   t->d_tabF = t->d_tabB = t->d_w = nullptr;
   t->d_kappa = t->d_partials = t->d_norms = nullptr;
   t->d_flags = nullptr; t->d_status = nullptr; t->h_status = nullptr; t->d_xs = t->d_bs = nullptr;
 }
 
-// choose z-slabs: one warp per face layer, at most 32 warps per CTA, the
-// shared-memory ring (4 levels x layers x (N/2+2) values) within ~200 KB
-void choose_slabs(ilu_tet t, int requested) {
-  const int N = t->host.N;
+// Partition for one substitution: wpl warps per face layer (one chunk of 32
+// rows each at the widest level), as many layers per slab as fit 31 compute
+// warps and ~200 KB of shared memory (ring, prefetch slots, row cache).
+// Thin slabs are the default: inside a cluster a hop between slabs costs a
+// few hundred cycles, while every extra layer adds its warps' issue time to
+// each level of the slab.
+WaveGeom pick_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
   const int layers = std::max(1, N - 3);
-  const size_t e = t->elem();
-  int zb = 16;
-  if (requested > 0) zb = (layers + requested - 1) / requested;
-  zb = std::max(1, std::min(zb, 32));
-  while (zb > 1 && (size_t)4 * zb * (N / 2 + 2) * e > 200 * 1024) zb /= 2;
+  WaveGeom g = {};
+  g.wpl = std::max(1, std::min(8, (N / 2 + 31) / 32));
+  const int max_warps = wave_uses_registers(kind, dx) ? 15 : 31;  // plus the communication warp
+  int zb = std::max(1, max_warps / g.wpl);
+  zb = std::min(zb, requested > 0 ? (layers + requested - 1) / requested : 2);
   zb = std::min(zb, layers);
-  t->slab_layers = zb;
-  t->nslabs = (layers + zb - 1) / zb;
+  while (zb > 1) {
+    g.zb = zb;
+    if (wave_smem_bytes(N, g, kind, dxp, fwd) <= 200 * 1024) break;
+    --zb;
+  }
+  g.zb = zb;
+  g.P = (layers + zb - 1) / zb;
+  return g;
+}
+
+void choose_geometry(ilu_tet t, int requested) {
+  const int N = t->host.N;
+  DevTet &d = t->dev;
+  d.fwd = pick_geom(N, t->kind(), t->host.rstride, t->host.dx, true, requested);
+  d.bwd = pick_geom(N, t->kind(), t->host.rstride, t->host.dx, false, requested);
+  d.fwd.prog = 0;
+  d.bwd.prog = d.fwd.P;
+  d.fwd.ticket = d.fwd.P + d.bwd.P;
+  d.bwd.ticket = d.fwd.ticket + 1;
+  t->nflags = d.fwd.P + d.bwd.P + 2;
+}
+
+// largest schedulable cluster per substitution kernel (one cluster holds the
+// whole tet when it has at most that many slabs)
+ilu_status choose_clusters(ilu_tet t) {
+  DevTet &d = t->dev;
+  int cf = 1, cb = 1;
+  d.fwd.csize = d.bwd.csize = 1;
+  CK(launch_forward(d, t->kind(), nullptr, 0, nullptr, &cf), "cluster query");
+  CK(launch_backward(d, t->kind(), nullptr, nullptr, 0, nullptr, &cb), "cluster query");
+  // as few clusters as the limit allows, as evenly filled as possible
+  d.fwd.csize = (d.fwd.P + (d.fwd.P + cf - 1) / cf - 1) / ((d.fwd.P + cf - 1) / cf);
+  d.bwd.csize = (d.bwd.P + (d.bwd.P + cb - 1) / cb - 1) / ((d.bwd.P + cb - 1) / cb);
+  return ILU_OK;
 }
 
 ilu_status upload(ilu_tet t) {
@@ -111,7 +154,7 @@ ilu_status upload(ilu_tet t) {
   CK(cudaSetDevice(t->device), "cudaSetDevice");
   const size_t nn = t->nnodes();
   const bool f64 = t->precision == ILU_F64;
-  const size_t nf = h.tabF64.size(), nb = h.tabB64.size();
+  const size_t nf = f64 ? h.tabF64.size() : h.tabF32.size(), nb = f64 ? h.tabB64.size() : h.tabB32.size();
   const size_t es = f64 ? sizeof(double) : sizeof(float);
   CK(cudaMalloc(&t->d_tabF, std::max<size_t>(nf, 1) * es), "cudaMalloc tables");
   CK(cudaMalloc(&t->d_tabB, std::max<size_t>(nb, 1) * es), "cudaMalloc tables");
@@ -125,8 +168,8 @@ ilu_status upload(ilu_tet t) {
   }
   CK(cudaMalloc(&t->d_w, nn * t->elem()), "cudaMalloc scratch");
   CK(cudaMemset(t->d_w, 0, nn * t->elem()), "cudaMemset scratch");
-  CK(cudaMalloc(&t->d_flags, sizeof(int) * (2 * t->nslabs + 2)), "cudaMalloc flags");
-  CK(cudaMemset(t->d_flags, 0, sizeof(int) * (2 * t->nslabs + 2)), "cudaMemset flags");
+  CK(cudaMalloc(&t->d_flags, sizeof(int) * t->nflags), "cudaMalloc flags");
+  CK(cudaMemset(t->d_flags, 0, sizeof(int) * t->nflags), "cudaMemset flags");
   CK(cudaMalloc(&t->d_status, sizeof(LaunchStatus)), "cudaMalloc status");
   CK(cudaMemset(t->d_status, 0, sizeof(LaunchStatus)), "cudaMemset status");
   CK(cudaMallocHost(&t->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
@@ -136,12 +179,11 @@ ilu_status upload(ilu_tet t) {
   t->norms_cap = 0;
   DevTet &d = t->dev;
   d.L = h.L; d.N = h.N; d.h = h.h; d.dx = h.dx; d.rstride = h.rstride;
-  d.nslabs = t->nslabs; d.slab_layers = t->slab_layers;
   d.const_kappa = h.const_kappa ? 1 : 0;
   d.tabF = t->d_tabF; d.tabB = t->d_tabB; d.kappa = t->d_kappa; d.w = t->d_w; d.flags = t->d_flags;
   std::memcpy(d.A15, h.A15, sizeof(d.A15));
   std::memcpy(d.Wstar, h.Wstar, sizeof(d.Wstar));
-  return ILU_OK;
+  return choose_clusters(t);
 }
 
 ilu_status upload_tables(ilu_tet t) {
@@ -149,12 +191,13 @@ ilu_status upload_tables(ilu_tet t) {
   CK(cudaSetDevice(t->device), "cudaSetDevice");
   const bool f64 = t->precision == ILU_F64;
   const size_t es = f64 ? sizeof(double) : sizeof(float);
-  if (h.tabF64.size())
-    CK(cudaMemcpy(t->d_tabF, f64 ? (const void *)h.tabF64.data() : (const void *)h.tabF32.data(),
-                  h.tabF64.size() * es, cudaMemcpyHostToDevice), "upload tables");
-  if (h.tabB64.size())
-    CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(),
-                  h.tabB64.size() * es, cudaMemcpyHostToDevice), "upload tables");
+  const size_t nf = f64 ? h.tabF64.size() : h.tabF32.size(), nb = f64 ? h.tabB64.size() : h.tabB32.size();
+  if (nf)
+    CK(cudaMemcpy(t->d_tabF, f64 ? (const void *)h.tabF64.data() : (const void *)h.tabF32.data(), nf * es,
+                  cudaMemcpyHostToDevice), "upload tables");
+  if (nb)
+    CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(), nb * es,
+                  cudaMemcpyHostToDevice), "upload tables");
   return ILU_OK;
 }
 
@@ -236,8 +279,7 @@ struct Traced {
 
 // one sweep on device vectors: residual into w, forward, backward with x += w
 ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStream_t st) {
-  const int P = t->nslabs;
-  CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * (2 * P + 2), st), "reset flags");
+  CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * t->nflags, st), "reset flags");
   int used = 0;
   {
     Traced tr(t, 0, st);
@@ -255,6 +297,46 @@ ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStre
     Traced tr(t, 2, st);
     CK(launch_backward(t->dev, t->kind(), x, t->d_status, t->max_spins, st), "backward launch");
   }
+  return ILU_OK;
+}
+
+// apply the preconditioner: z = C~^{-1} r on the interior (z's boundary 0)
+ilu_status precond(ilu_tet t, const void *r, void *z, cudaStream_t st) {
+  const long long n = (long long)t->nnodes();
+  const bool vf64 = t->precision != ILU_F32;   // Krylov vectors
+  const bool wf64 = t->precision == ILU_F64;   // sweep scratch
+  CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * t->nflags, st), "reset flags");
+  CK(launch_copy(vf64, wf64, r, t->d_w, n, st), "copy launch");
+  CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
+  {
+    Traced tr(t, 1, st);
+    CK(launch_forward(t->dev, t->kind(), t->d_status, t->max_spins, st), "forward launch");
+  }
+  {
+    Traced tr(t, 2, st);
+    CK(launch_backward(t->dev, t->kind(), z, t->d_status, t->max_spins, st), "backward launch");
+  }
+  return ILU_OK;
+}
+
+ilu_status ensure_krylov(ilu_tet t) {
+  if (t->d_r) return ILU_OK;
+  const size_t bytes = t->nnodes() * t->elem();
+  for (void **v : {&t->d_r, &t->d_z, &t->d_p, &t->d_q, &t->d_zero}) {
+    CK(cudaMalloc(v, bytes), "cudaMalloc Krylov vectors");
+    CK(cudaMemset(*v, 0, bytes), "cudaMemset Krylov vectors");
+  }
+  CK(cudaMalloc(&t->d_dot, sizeof(double) * kDotPartials), "cudaMalloc dot partials");
+  CK(cudaMalloc(&t->d_scal, sizeof(double) * 8), "cudaMalloc scalars");
+  CK(cudaMallocHost(&t->h_scal, sizeof(double) * 8), "cudaMallocHost scalars");
+  return ILU_OK;
+}
+
+// read n device scalars (synchronising the stream)
+ilu_status read_scalars(ilu_tet t, int n, cudaStream_t st) {
+  CK(cudaMemcpyAsync(t->h_scal, t->d_scal, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "scalar copy");
+  CK(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (t->h_status && t->h_status->code) return fail(ILU_ETIMEOUT, "a bounded device wait ran out");
   return ILU_OK;
 }
 
@@ -334,7 +416,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
       delete t;
       return fail(ILU_ENODEV, "no CUDA device with that ordinal");
     }
-    choose_slabs(t, o.slabs);
+    choose_geometry(t, o.slabs);
     st = upload(t);
     if (st != ILU_OK) {
       free_device(t);
@@ -484,6 +566,94 @@ ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double
     CK(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   }
   return ILU_OK;
+}
+
+ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
+                     int *iters, double *rel_res) {
+  ilu_status st = check_usable(t);
+  if (st != ILU_OK) return st;
+  if (!x || !b) return fail(ILU_EINVAL, "null vector");
+  if (method != ILU_RICHARDSON && method != ILU_PCG) return fail(ILU_EINVAL, "unknown method");
+  if (!(rtol >= 0.0) || max_iter < 0) return fail(ILU_EINVAL, "bad tolerance or iteration limit");
+  std::lock_guard<std::mutex> lk(t->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaSetDevice(t->device), "cudaSetDevice");
+  st = ensure_krylov(t);
+  if (st != ILU_OK) return st;
+  const int N = t->host.N;
+  const long long n = (long long)t->nnodes();
+  const bool vf64 = t->precision != ILU_F32;
+  const int vkind = vf64 ? kSweepF64 : kSweepF32;  // residual into a Krylov-typed vector
+  if (iters) *iters = 0;
+  if (rel_res) *rel_res = 0.0;
+  // ||b|| over the interior
+  CK(cudaMemcpyAsync(t->h_status, t->d_status, sizeof(LaunchStatus), cudaMemcpyDeviceToHost, s), "status copy");
+  CK(launch_interior_norm(N, vf64, b, t->d_partials, t->nblocks, t->d_scal, s), "norm launch");
+  st = read_scalars(t, 1, s);
+  if (st != ILU_OK) return st;
+  double bn = t->h_scal[0];
+  if (bn == 0.0) bn = 1.0;
+  auto residual_norm = [&](double &rel) -> ilu_status {  // r = b - A x, rel = ||r|| / ||b||
+    int used = 0;
+    CK(launch_residual(t->dev, vkind, x, b, t->d_r, t->d_partials, t->nblocks, &used, s), "residual launch");
+    CK(launch_norm_finish(t->d_partials, used, t->d_scal, s), "norm launch");
+    CK(cudaMemcpyAsync(t->h_status, t->d_status, sizeof(LaunchStatus), cudaMemcpyDeviceToHost, s), "status copy");
+    ilu_status e = read_scalars(t, 1, s);
+    rel = t->h_scal[0] / bn;
+    return e;
+  };
+  double rel = 0.0;
+  if (method == ILU_RICHARDSON) {
+    // defect correction: r in FP64 (MIXED/F64), correction C~^{-1} r in the sweep precision
+    for (int it = 0;; ++it) {
+      st = residual_norm(rel);
+      if (st != ILU_OK) { t->failed = true; return st; }
+      if (iters) *iters = it;
+      if (rel_res) *rel_res = rel;
+      if (rel <= rtol) return ILU_OK;
+      if (it == max_iter) return fail(ILU_ENOTCONV, "Richardson iteration reached max_iter");
+      st = precond(t, t->d_r, t->d_z, s);
+      if (st != ILU_OK) { t->failed = true; return st; }
+      CK(launch_axpy(vf64, x, t->d_z, 1.0, n, s), "axpy launch");
+    }
+  }
+  // preconditioned conjugate gradients on the interior system
+  st = residual_norm(rel);
+  if (st != ILU_OK) { t->failed = true; return st; }
+  double rz_old = 0.0;
+  for (int it = 0;; ++it) {
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = rel;
+    if (rel <= rtol) return ILU_OK;
+    if (it == max_iter) return fail(ILU_ENOTCONV, "PCG reached max_iter");
+    st = precond(t, t->d_r, t->d_z, s);
+    if (st != ILU_OK) { t->failed = true; return st; }
+    CK(launch_dot(vf64, t->d_r, t->d_z, n, t->d_dot, t->d_scal, s), "dot launch");
+    st = read_scalars(t, 1, s);
+    if (st != ILU_OK) { t->failed = true; return st; }
+    const double rz = t->h_scal[0];
+    if (it == 0)
+      CK(launch_copy(vf64, vf64, t->d_z, t->d_p, n, s), "copy launch");
+    else
+      CK(launch_xpay(vf64, t->d_p, t->d_z, rz / rz_old, n, s), "xpay launch");
+    rz_old = rz;
+    // q = -A p (the residual kernel with b = 0; p vanishes on the boundary)
+    int used = 0;
+    CK(launch_residual(t->dev, vkind, t->d_p, t->d_zero, t->d_q, t->d_partials, t->nblocks, &used, s),
+       "matvec launch");
+    CK(launch_dot(vf64, t->d_p, t->d_q, n, t->d_dot, t->d_scal, s), "dot launch");
+    st = read_scalars(t, 1, s);
+    if (st != ILU_OK) { t->failed = true; return st; }
+    const double pAp = -t->h_scal[0];
+    if (!(pAp > 0.0)) return fail(ILU_ESINGULAR, "PCG met a non-positive curvature");
+    const double alpha = rz / pAp;
+    CK(launch_axpy(vf64, x, t->d_p, alpha, n, s), "axpy launch");
+    CK(launch_axpy(vf64, t->d_r, t->d_q, alpha, n, s), "axpy launch");  // r -= alpha A p
+    CK(launch_dot(vf64, t->d_r, t->d_r, n, t->d_dot, t->d_scal, s), "dot launch");
+    st = read_scalars(t, 1, s);
+    if (st != ILU_OK) { t->failed = true; return st; }
+    rel = std::sqrt(std::max(t->h_scal[0], 0.0)) / bn;
+  }
 }
 
 ilu_status ilu_profile_enable(ilu_tet t, int enable) {

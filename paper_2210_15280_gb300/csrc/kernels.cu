@@ -1,23 +1,16 @@
 // kernels.cu -- sweep kernels of the matrix-free surrogate ILU(0) smoother
 // (arXiv 2210.15280, Alg. 2, V2 boundary rule) for sm_103a.
 //
-// One sweep is three launches:
+// One sweep is three launches: this file holds the first,
 //   residual   r = b - A x on every interior point, fully parallel (one warp
 //              per grid row, coalesced along x); the operator is the constant
 //              15-point stencil or is assembled on the fly from kappa at the
-//              grid points (edge-star weights); FP64 for F64/MIXED.
-//   forward    w = L~^{-1} r  (in place), level-scheduled on the hyperplanes
-//              x + 2y + 3z = s: every lower direction has a negative hyperplane
-//              weight, so the points of one level are independent.
-//   backward   w = L~^{-T} D~^{-1} w, x += w, the same levels in reverse.
-// The wavefront kernels split the tet into z-slabs, one CTA per slab and one
-// warp per face layer.  The last three levels of w of the slab stay in a
-// shared-memory ring; the layer just outside the slab is read from global
-// memory after the neighbouring slab has published its progress.  CTAs take
-// slab numbers from an atomic ticket in dependency order, so a CTA only ever
-// waits for CTAs that are already running; every wait is bounded.
+//              grid points (edge-star weights); FP64 for F64/MIXED,
+// and the deterministic norm reduction; wavefront.cu holds the forward and
+// backward substitutions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <utility>
 
@@ -42,47 +35,6 @@ __device__ __forceinline__ void star_all(std::integer_sequence<int, E...>, doubl
 }
 
 // --------------------------------------------------------- small helpers --
-
-__device__ __forceinline__ int ylo_of(int N, int s, int z) { return max(1, s - 2 * z - N + 1); }
-__device__ __forceinline__ int yhi_of(int s, int z) {
-  const int v = s - 3 * z - 1;
-  return v < 0 ? 0 : v >> 1;
-}
-
-__device__ __forceinline__ int ld_acquire(const int *p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release(int *p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ T horner(const T *c, int n, T t) {
-  T v = c[n];
-  for (int k = n - 1; k >= 0; --k) v = fma(v, t, c[k]);
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T ldcg(const T *p) {
-  return __ldcg(p);
-}
-
-// Bounded wait of thread 0 for flags[idx] >= target.  Returns false on timeout.
-__device__ bool wait_flag(const int *flag, int target, int &seen, long long max_spins) {
-  if (seen >= target) return true;
-  long long spins = 0;
-  int v = ld_acquire(flag);
-  while (v < target) {
-    if (++spins > max_spins) return false;
-    __nanosleep(32);
-    v = ld_acquire(flag);
-  }
-  seen = v;
-  return true;
-}
 
 // --------------------------------------------------------------- residual --
 
@@ -173,6 +125,85 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
   }
 }
 
+// ------------------------------------------------- solver vector helpers --
+// (full-grid vectors whose boundary entries are zero, except x)
+
+constexpr int kVecBlocks = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(256) vec_dot_kernel(const T *__restrict__ a, const T *__restrict__ b, long long n,
+                                                      double *__restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    acc += (double)a[i] * (double)b[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// y += a x
+template <typename T>
+__global__ void vec_axpy_kernel(T *__restrict__ y, const T *__restrict__ x, double a, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (T)fma(a, (double)x[i], (double)y[i]);
+}
+
+// p = z + b p
+template <typename T>
+__global__ void vec_xpay_kernel(T *__restrict__ p, const T *__restrict__ z, double b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = (T)fma(b, (double)p[i], (double)z[i]);
+}
+
+template <typename TI, typename TO>
+__global__ void vec_copy_kernel(TO *__restrict__ dst, const TI *__restrict__ src, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (TO)src[i];
+}
+
+// sum of squares of v over the interior points (rows as in the residual)
+template <typename T>
+__global__ void __launch_bounds__(256) interior_sq_kernel(int N, const T *__restrict__ v, double *__restrict__ partials) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int z = blockIdx.y + 1;
+  const int y = blockIdx.x * 8 + warp + 1;
+  double acc = 0.0;
+  if (y + z <= N - 2) {
+    const int64_t r0 = grid_index(N, 0, y, z);
+    for (int xx = 1 + lane; xx <= N - 1 - y - z; xx += 32) acc += (double)v[r0 + xx] * (double)v[r0 + xx];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += red[k];
+    partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_finish_kernel(const double *__restrict__ partials, int n, double *out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 __global__ void norm_finish_kernel(const double *__restrict__ partials, int n, double *out) {
   __shared__ double red[256];
   double s = 0.0;
@@ -186,224 +217,11 @@ __global__ void norm_finish_kernel(const double *__restrict__ partials, int n, d
   if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
-// ---------------------------------------------------------------- forward --
-
-// In-place forward substitution w <- L~^{-1} w for the interior of one tet.
-template <typename TW>
-__global__ void __launch_bounds__(1024) forward_kernel(DevTet t, LaunchStatus *status, long long max_spins) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TW *ring = reinterpret_cast<TW *>(smem_raw);
-  __shared__ int s_slab, s_abort;
-  const int N = t.N, Zb = t.slab_layers, P = t.nslabs;
-  const int RC = N / 2 + 2;
-  int *flags = t.flags;
-  if (threadIdx.x == 0) {
-    s_slab = atomicAdd(&flags[2 * P], 1);
-    s_abort = 0;
-  }
-  __syncthreads();
-  const int k = s_slab;
-  if (k >= P) return;
-  const int zs = 1 + k * Zb, ze = min(zs + Zb, N - 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = zs + warp;
-  const bool active = z < ze;
-  const int s_begin = 3 * zs + 3, s_end = 2 * N + ze - 4;
-  const TW *tab = reinterpret_cast<const TW *>(t.tabF);
-  TW *wg = reinterpret_cast<TW *>(t.w);
-  const int S = t.rstride, dxg = t.dx;
-  const TW hh = (TW)(0.5 * t.h);
-  int seen = 0;
-  if (threadIdx.x == 0 && k > 0) {
-    if (!wait_flag(&flags[k - 1], s_begin, seen, max_spins)) {
-      s_abort = 1;
-      atomicCAS(&status->code, 0, 6);
-      status->where = k;
-      status->level = s_begin;
-    }
-  }
-  __syncthreads();
-  for (int s = s_begin; s <= s_end && !s_abort; ++s) {
-    if (active) {
-      const int ylo = ylo_of(N, s, z), yhi = yhi_of(s, z);
-      TW *slot = ring + ((size_t)(s & 3) * Zb + warp) * RC;
-      const TW *m1 = ring + ((size_t)((s - 1) & 3) * Zb + warp) * RC;
-      const TW *m2 = ring + ((size_t)((s - 2) & 3) * Zb + warp) * RC;
-      const bool halo = (warp == 0);  // layer z-1 belongs to the previous slab
-      const TW *b1 = halo ? nullptr : ring + ((size_t)((s - 1) & 3) * Zb + warp - 1) * RC;
-      const TW *b2 = halo ? nullptr : ring + ((size_t)((s - 2) & 3) * Zb + warp - 1) * RC;
-      const TW *b3 = halo ? nullptr : ring + ((size_t)((s - 3) & 3) * Zb + warp - 1) * RC;
-      const int ylo1 = ylo_of(N, s - 1, z), ylo2 = ylo_of(N, s - 2, z);
-      const int zl1 = ylo_of(N, s - 1, z - 1), zl2 = ylo_of(N, s - 2, z - 1), zl3 = ylo_of(N, s - 3, z - 1);
-      for (int y = ylo + lane; y <= yhi; y += 32) {
-        const int x = s - 2 * y - 3 * z;
-        const int64_t gi = grid_index(N, x, y, z);
-        const TW *c = tab + (size_t)row_id(N, y, z) * 7 * S;
-        const TW tt = (TW)(2 * x - (N - y - z)) * hh;
-        TW acc = wg[gi];
-        if (x >= 2) acc = fma(-horner(c + 0 * S, dxg, tt), m1[y - ylo1], acc);
-        if (y >= 2) {
-          acc = fma(-horner(c + 1 * S, dxg, tt), m2[y - 1 - ylo2], acc);
-          acc = fma(-horner(c + 2 * S, dxg, tt), m1[y - 1 - ylo1], acc);
-        }
-        if (z >= 2) {
-          TW vbnw = 0, vbn, vbc, vbe;
-          if (halo) {
-            if (x >= 2) vbnw = ldcg(wg + grid_index(N, x - 1, y + 1, z - 1));
-            vbn = ldcg(wg + grid_index(N, x, y + 1, z - 1));
-            vbc = ldcg(wg + grid_index(N, x, y, z - 1));
-            vbe = ldcg(wg + grid_index(N, x + 1, y, z - 1));
-          } else {
-            if (x >= 2) vbnw = b2[y + 1 - zl2];
-            vbn = b1[y + 1 - zl1];
-            vbc = b3[y - zl3];
-            vbe = b2[y - zl2];
-          }
-          if (x >= 2) acc = fma(-horner(c + 3 * S, dxg, tt), vbnw, acc);
-          acc = fma(-horner(c + 4 * S, dxg, tt), vbn, acc);
-          acc = fma(-horner(c + 5 * S, dxg, tt), vbc, acc);
-          acc = fma(-horner(c + 6 * S, dxg, tt), vbe, acc);
-        }
-        slot[y - ylo] = acc;
-        wg[gi] = acc;
-      }
-    }
-    if (threadIdx.x == 0) {
-      if (k + 1 < P) {
-        __threadfence();
-        st_release(&flags[k], s);  // levels <= s-1 complete (barrier of the previous iteration)
-      }
-      if (k > 0 && s < s_end && !wait_flag(&flags[k - 1], s + 1, seen, max_spins)) {
-        s_abort = 1;
-        atomicCAS(&status->code, 0, 6);
-        status->where = k;
-        status->level = s + 1;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && k + 1 < P) {
-    __threadfence();
-    st_release(&flags[k], INT_MAX / 2);
-  }
-}
-
-// --------------------------------------------------------------- backward --
-
-// w <- D~^{-1} w - sum_d L~^{p-d}_d w^{p-d} in reverse level order, x += w.
-template <typename TW, typename TX>
-__global__ void __launch_bounds__(1024) backward_kernel(DevTet t, TX *__restrict__ xg, LaunchStatus *status,
-                                                        long long max_spins) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TW *ring = reinterpret_cast<TW *>(smem_raw);
-  __shared__ int s_slab, s_abort;
-  const int N = t.N, Zb = t.slab_layers, P = t.nslabs;
-  const int RC = N / 2 + 2;
-  int *flags = t.flags + P;  // backward progress words
-  if (threadIdx.x == 0) {
-    s_slab = P - 1 - atomicAdd(&t.flags[2 * P + 1], 1);
-    s_abort = 0;
-  }
-  __syncthreads();
-  const int k = s_slab;
-  if (k < 0) return;
-  const int zs = 1 + k * Zb, ze = min(zs + Zb, N - 2);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = zs + warp;
-  const bool active = z < ze;
-  const int s_begin = 3 * zs + 3, s_end = 2 * N + ze - 4;
-  const int TOP = 3 * N + 1;  // progress value for "level s done" is TOP - s
-  const TW *tab = reinterpret_cast<const TW *>(t.tabB);
-  TW *wg = reinterpret_cast<TW *>(t.w);
-  const int S = t.rstride, dxg = t.dx;
-  const TW hh = (TW)(0.5 * t.h);
-  int seen = 0;
-  if (threadIdx.x == 0 && k + 1 < P) {
-    if (!wait_flag(&flags[k + 1], TOP - (s_end + 1), seen, max_spins)) {
-      s_abort = 1;
-      atomicCAS(&status->code, 0, 6);
-      status->where = k;
-      status->level = s_end;
-    }
-  }
-  __syncthreads();
-  for (int s = s_end; s >= s_begin && !s_abort; --s) {
-    if (active) {
-      const int ylo = ylo_of(N, s, z), yhi = yhi_of(s, z);
-      TW *slot = ring + ((size_t)(s & 3) * Zb + warp) * RC;
-      const TW *p1 = ring + ((size_t)((s + 1) & 3) * Zb + warp) * RC;
-      const TW *p2 = ring + ((size_t)((s + 2) & 3) * Zb + warp) * RC;
-      const bool halo = (warp == Zb - 1) || (z + 1 >= ze);  // layer z+1 belongs to the next slab
-      const TW *u1 = halo ? nullptr : ring + ((size_t)((s + 1) & 3) * Zb + warp + 1) * RC;
-      const TW *u2 = halo ? nullptr : ring + ((size_t)((s + 2) & 3) * Zb + warp + 1) * RC;
-      const TW *u3 = halo ? nullptr : ring + ((size_t)((s + 3) & 3) * Zb + warp + 1) * RC;
-      const int ylo1 = ylo_of(N, s + 1, z), ylo2 = ylo_of(N, s + 2, z);
-      const int zl1 = ylo_of(N, s + 1, z + 1), zl2 = ylo_of(N, s + 2, z + 1), zl3 = ylo_of(N, s + 3, z + 1);
-      for (int y = ylo + lane; y <= yhi; y += 32) {
-        const int x = s - 2 * y - 3 * z;
-        const int64_t gi = grid_index(N, x, y, z);
-        const TW *c = tab + (size_t)row_id(N, y, z) * 8 * S;
-        const TW tt = (TW)(2 * x - (N - y - z)) * hh;
-        TW acc = horner(c, dxg, tt) * wg[gi];
-        const bool inner = x + y + z <= N - 2;  // p - w, p - s, p - bc interior
-        if (inner) {
-          acc = fma(-horner(c + 1 * S, dxg, tt), p1[y - ylo1], acc);        // p - w  = (x+1, y, z)
-          acc = fma(-horner(c + 2 * S, dxg, tt), p2[y + 1 - ylo2], acc);    // p - s  = (x, y+1, z)
-        }
-        if (x >= 2) acc = fma(-horner(c + 3 * S, dxg, tt), p1[y + 1 - ylo1], acc);  // p - se = (x-1, y+1, z)
-        // upper layer z+1
-        TW vbnw = 0, vbn = 0, vbc = 0, vbe = 0;
-        const bool has_bnw = (y >= 2) && inner, has_bn = (y >= 2), has_bc = inner, has_be = (x >= 2);
-        if (halo) {
-          if (has_bnw) vbnw = ldcg(wg + grid_index(N, x + 1, y - 1, z + 1));
-          if (has_bn) vbn = ldcg(wg + grid_index(N, x, y - 1, z + 1));
-          if (has_bc) vbc = ldcg(wg + grid_index(N, x, y, z + 1));
-          if (has_be) vbe = ldcg(wg + grid_index(N, x - 1, y, z + 1));
-        } else {
-          if (has_bnw) vbnw = u2[y - 1 - zl2];
-          if (has_bn) vbn = u1[y - 1 - zl1];
-          if (has_bc) vbc = u3[y - zl3];
-          if (has_be) vbe = u2[y - zl2];
-        }
-        if (has_bnw) acc = fma(-horner(c + 4 * S, dxg, tt), vbnw, acc);
-        if (has_bn) acc = fma(-horner(c + 5 * S, dxg, tt), vbn, acc);
-        if (has_bc) acc = fma(-horner(c + 6 * S, dxg, tt), vbc, acc);
-        if (has_be) acc = fma(-horner(c + 7 * S, dxg, tt), vbe, acc);
-        slot[y - ylo] = acc;
-        wg[gi] = acc;
-        xg[gi] = xg[gi] + (TX)acc;
-      }
-    }
-    if (threadIdx.x == 0) {
-      if (k > 0) {
-        __threadfence();
-        st_release(&flags[k], TOP - (s + 1));  // levels >= s+1 complete
-      }
-      if (k + 1 < P && s > s_begin && !wait_flag(&flags[k + 1], TOP - s, seen, max_spins)) {
-        s_abort = 1;
-        atomicCAS(&status->code, 0, 6);
-        status->where = k;
-        status->level = s - 1;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && k > 0) {
-    __threadfence();
-    st_release(&flags[k], INT_MAX / 2);
-  }
-}
-
 }  // namespace
 
 // ------------------------------------------------------------ launchers --
 
 int residual_blocks(int N) { return ((N - 3 + 7) / 8) * (N - 3); }
-
-size_t sweep_smem_bytes(int N, int slab_layers, int kind) {
-  const size_t e = kind == kSweepF64 ? sizeof(double) : sizeof(float);
-  return (size_t)4 * slab_layers * (N / 2 + 2) * e;
-}
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st) {
@@ -437,40 +255,65 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
   return cudaGetLastError();
 }
 
+template <typename T>
+static unsigned vec_blocks(long long n) {
+  return (unsigned)std::min<long long>((n + 255) / 256, 4096);
+}
+
+cudaError_t launch_dot(bool f64, const void *a, const void *b, long long n, double *partials, double *out,
+                       cudaStream_t st) {
+  if (f64)
+    vec_dot_kernel<double><<<kVecBlocks, 256, 0, st>>>((const double *)a, (const double *)b, n, partials);
+  else
+    vec_dot_kernel<float><<<kVecBlocks, 256, 0, st>>>((const float *)a, (const float *)b, n, partials);
+  sum_finish_kernel<<<1, 256, 0, st>>>(partials, kVecBlocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(bool f64, void *y, const void *x, double a, long long n, cudaStream_t st) {
+  if (f64)
+    vec_axpy_kernel<double><<<vec_blocks<double>(n), 256, 0, st>>>((double *)y, (const double *)x, a, n);
+  else
+    vec_axpy_kernel<float><<<vec_blocks<float>(n), 256, 0, st>>>((float *)y, (const float *)x, a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xpay(bool f64, void *p, const void *z, double b, long long n, cudaStream_t st) {
+  if (f64)
+    vec_xpay_kernel<double><<<vec_blocks<double>(n), 256, 0, st>>>((double *)p, (const double *)z, b, n);
+  else
+    vec_xpay_kernel<float><<<vec_blocks<float>(n), 256, 0, st>>>((float *)p, (const float *)z, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(bool src_f64, bool dst_f64, const void *src, void *dst, long long n, cudaStream_t st) {
+  const unsigned g = vec_blocks<double>(n);
+  if (src_f64 && dst_f64)
+    vec_copy_kernel<double, double><<<g, 256, 0, st>>>((double *)dst, (const double *)src, n);
+  else if (src_f64)
+    vec_copy_kernel<double, float><<<g, 256, 0, st>>>((float *)dst, (const double *)src, n);
+  else if (dst_f64)
+    vec_copy_kernel<float, double><<<g, 256, 0, st>>>((double *)dst, (const float *)src, n);
+  else
+    vec_copy_kernel<float, float><<<g, 256, 0, st>>>((float *)dst, (const float *)src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interior_norm(int N, bool f64, const void *v, double *partials, int cap, double *out,
+                                 cudaStream_t st) {
+  dim3 grid((N - 3 + 7) / 8, N - 3);
+  if ((int)(grid.x * grid.y) > cap) return cudaErrorInvalidValue;
+  if (f64)
+    interior_sq_kernel<double><<<grid, 256, 0, st>>>(N, (const double *)v, partials);
+  else
+    interior_sq_kernel<float><<<grid, 256, 0, st>>>(N, (const float *)v, partials);
+  norm_finish_kernel<<<1, 256, 0, st>>>(partials, grid.x * grid.y, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm_finish(const double *partials, int n, double *out, cudaStream_t st) {
   norm_finish_kernel<<<1, 256, 0, st>>>(partials, n, out);
   return cudaGetLastError();
-}
-
-template <typename TW>
-static cudaError_t fwd_impl(const DevTet &t, LaunchStatus *status, long long max_spins, cudaStream_t st) {
-  const size_t smem = (size_t)4 * t.slab_layers * (t.N / 2 + 2) * sizeof(TW);
-  cudaError_t e = cudaFuncSetAttribute(forward_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  forward_kernel<TW><<<t.nslabs, 32 * t.slab_layers, smem, st>>>(t, status, max_spins);
-  return cudaGetLastError();
-}
-
-template <typename TW, typename TX>
-static cudaError_t bwd_impl(const DevTet &t, void *x, LaunchStatus *status, long long max_spins, cudaStream_t st) {
-  const size_t smem = (size_t)4 * t.slab_layers * (t.N / 2 + 2) * sizeof(TW);
-  cudaError_t e =
-      cudaFuncSetAttribute(backward_kernel<TW, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  backward_kernel<TW, TX><<<t.nslabs, 32 * t.slab_layers, smem, st>>>(t, (TX *)x, status, max_spins);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_forward(const DevTet &t, int kind, LaunchStatus *status, long long max_spins, cudaStream_t st) {
-  if (kind == kSweepF64) return fwd_impl<double>(t, status, max_spins, st);
-  return fwd_impl<float>(t, status, max_spins, st);
-}
-
-cudaError_t launch_backward(const DevTet &t, int kind, void *x, LaunchStatus *status, long long max_spins,
-                            cudaStream_t st) {
-  if (kind == kSweepF64) return bwd_impl<double, double>(t, x, status, max_spins, st);
-  if (kind == kSweepMixed) return bwd_impl<float, double>(t, x, status, max_spins, st);
-  return bwd_impl<float, float>(t, x, status, max_spins, st);
 }
 
 }  // namespace ilu

@@ -247,7 +247,9 @@ void build_row_tables(HostTet &t) {
   const int N = t.N;
   const int64_t R = num_rows(N);
   t.dx = t.deg[0];
-  t.rstride = t.dx + 1;
+  // coefficients per function, zero padded to 4, 8 or 16 so that a row block
+  // is a whole number of 16-byte chunks and Horner can run over the padding
+  t.rstride = t.dx + 1 <= 4 ? 4 : (t.dx + 1 <= 8 ? 8 : 16);
   const int S = t.rstride;
   t.tabF64.assign((size_t)R * 7 * S, 0.0);
   t.tabB64.assign((size_t)R * 8 * S, 0.0);
@@ -269,8 +271,18 @@ void build_row_tables(HostTet &t) {
     if (a < b) pool.emplace_back(work, a, b);
   }
   for (auto &th : pool) th.join();
-  t.tabF32.assign(t.tabF64.begin(), t.tabF64.end());
-  t.tabB32.assign(t.tabB64.begin(), t.tabB64.end());
+  // FP32 tables: four function pairs per row, coefficient k of functions
+  // (2p, 2p+1) side by side, so that the sweep evaluates two polynomials per
+  // packed FMA; the forward table gets a zero eighth function
+  t.tabF32.assign((size_t)R * 8 * S, 0.0f);
+  t.tabB32.assign((size_t)R * 8 * S, 0.0f);
+  for (int64_t r = 0; r < R; ++r)
+    for (int f = 0; f < 8; ++f)
+      for (int k = 0; k < S; ++k) {
+        const size_t o = (((size_t)r * 4 + f / 2) * S + k) * 2 + (f & 1);
+        if (f < 7) t.tabF32[o] = (float)t.tabF64[((size_t)r * 7 + f) * S + k];
+        t.tabB32[o] = (float)t.tabB64[((size_t)r * 8 + f) * S + k];
+      }
 }
 
 static double horner(const double *c, int n, double tt) {

@@ -33,7 +33,7 @@ struct HostTet {
   int dx = 0;                  // x-degree = row polynomial degree
   int rstride = 0;             // padded coefficients per function in the row tables
   std::vector<double> tabF64, tabB64;  // rows x 7 x rstride, rows x 8 x rstride
-  std::vector<float> tabF32, tabB32;
+  std::vector<float> tabF32, tabB32;   // rows x 4 pairs x rstride x 2 (see build_row_tables)
 };
 
 // Full set-up.  Returns ILU_OK or an error with a message in err.

@@ -1,7 +1,6 @@
 // Temporary: entry points not built yet report ILU_EINVAL.
 #include "../../include/ilu.h"
 extern "C" {
-ilu_status ilu_solve(ilu_tet, void *, const void *, int, double, int, void *, int *, double *) { return ILU_EINVAL; }
 ilu_status ilu_batch_create(const ilu_tet *, int, const ilu_opts *, ilu_batch *) { return ILU_EINVAL; }
 ilu_status ilu_batch_destroy(ilu_batch) { return ILU_OK; }
 ilu_status ilu_batch_smooth(ilu_batch, void *const *, const void *const *, int, void *) { return ILU_EINVAL; }

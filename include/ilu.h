@@ -155,6 +155,21 @@ ilu_status ilu_smooth_host(ilu_tet t, void *x_host, const void *b_host, int swee
  * ||r||_2 and makes the call synchronous. */
 ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double *norm2, void *stream);
 
+/* r = b - A x and ||r||_2 like ilu_residual, for callers that cannot let a
+ * library allocate device memory (a framework's caching allocator or a fixed
+ * serving pool owns it, or cudaMalloc's implicit synchronisation is not
+ * acceptable).  The paper has no counterpart.  The caller passes x, b (device,
+ * the handle's vector type), r (device, same type; required: boundary entries
+ * set to 0) and norm_dev (device, one double receiving ||r||_2).  The only
+ * scratch, the per-block partial sums of the norm, lives in a fixed 512 KiB
+ * device array inside the library: levels above 9 are rejected with
+ * ILU_EINVAL.  The array is shared by all calls on a device and keeps the last
+ * call's contents (every entry used is written before it is read); calls whose
+ * kernels overlap on the GPU race on it and must be serialised.  The first
+ * call on a device looks up the array's device address; make that first call
+ * before any stream capture.  Asynchronous on `stream`; calls no allocator. */
+ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void *b, void *r, double *norm_dev, void *stream);
+
 typedef enum { ILU_RICHARDSON = 0, ILU_PCG = 1 } ilu_method;
 
 /* Solve A x = b on the interior (boundary of x = Dirichlet data) to

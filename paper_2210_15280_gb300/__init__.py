@@ -30,7 +30,7 @@ EXPORTS = [
     "ilu_smooth_host", "ilu_residual", "ilu_solve", "ilu_batch_create", "ilu_batch_destroy",
     "ilu_batch_smooth", "ilu_server_create", "ilu_server_submit", "ilu_server_wait", "ilu_server_release",
     "ilu_server_stats", "ilu_server_destroy", "ilu_num_nodes", "ilu_num_interior", "ilu_index",
-    "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read",
+    "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read", "ilu_residual_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def lib():
         L.ilu_smooth.argtypes = [vp, vp, vp, i, vp, vp]
         L.ilu_smooth_host.argtypes = [vp, vp, vp, i, vp]
         L.ilu_residual.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.ilu_residual_noalloc.argtypes = [vp, vp, vp, vp, vp, vp]
         L.ilu_solve.argtypes = [vp, vp, vp, i, d, i, vp, vp, vp]
         L.ilu_batch_create.argtypes = [vp, i, P(Opts), P(vp)]
         L.ilu_batch_destroy.argtypes = [vp]
@@ -231,6 +232,10 @@ class Tet:
         nrm = np.zeros(1)
         _check(lib().ilu_residual(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(nrm), _stream(stream)))
         return float(nrm[0])
+
+    def residual_noalloc(self, x, b, r, norm_dev, stream=None):
+        """r = b - A x and ||r|| into the device double norm_dev; no allocation."""
+        _check(lib().ilu_residual_noalloc(self.h, _ptr(x), _ptr(b), _ptr(r), _ptr(norm_dev), _stream(stream)))
 
     def solve(self, x, b, method=RICHARDSON, rtol=1e-8, max_iter=100000, stream=None):
         it = ctypes.c_int(0)

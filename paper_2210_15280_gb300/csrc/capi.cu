@@ -342,6 +342,18 @@ ilu_status read_scalars(ilu_tet t, int n, cudaStream_t st) {
 
 }  // namespace
 
+namespace ilu {
+// read-only view of a handle's device data for ilu_residual_noalloc
+const DevTet *tet_dev_view(ilu_tet t, int *device, int *precision, size_t *nnodes) {
+  if (!t) return nullptr;
+  *device = t->device;
+  *precision = t->precision;
+  *nnodes = t->nnodes();
+  return t->device >= 0 ? &t->dev : nullptr;
+}
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace ilu
+
 extern "C" {
 
 ilu_status ilu_opts_default(ilu_opts *o) {

@@ -183,15 +183,26 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 
 /* ----------------------------------------------------------------- batch -- */
 
-/* Group tets (same precision, any levels and degrees) for one persistent
- * launch per sweep.  The batch keeps references to the tets, which must
- * outlive it. */
+/* Group tets for smoothing together.  All tets must live on one device and
+ * share one precision; levels and degrees may differ.  opts (nullable) may set
+ * slabs (wavefront partition, as in ilu_setup) and max_wait_spins.  The batch
+ * keeps references to the tets, which must outlive it; it reuses each tet's
+ * scratch, so a tet must not be smoothed by another call while a batch call
+ * on it runs.  ILU_EINVAL for an empty batch, a null or failed tet, or mixed
+ * devices or precisions.  The paper smooths one macro-tet at a time; batching
+ * is this library's. */
 ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, ilu_batch *out);
 ilu_status ilu_batch_destroy(ilu_batch b);
 
-/* One call smooths every tet of the batch `sweeps` times: x[i], b[i] are
- * device vectors of tet i.  The sweep kernels are launched once per pass for
- * the whole batch (captured in a CUDA graph after the first call). */
+/* `sweeps` sweeps of Alg. 2 on every tet of the batch: x[i], b[i] (host
+ * arrays of n device pointers) are tet i's full-grid vectors, as for
+ * ilu_smooth.  A pass is one residual launch over all tets and, per group of
+ * tets with equal level and row layout, one forward and one backward launch;
+ * the groups' launches run concurrently.  The passes are captured in a CUDA
+ * graph on the first call (again when `sweeps` changes) and replayed on
+ * `stream`.  Synchronises `stream` before returning, to report a timed-out
+ * wait (ILU_ETIMEOUT, the batch is then failed and must be destroyed).
+ * Results equal ilu_smooth on each tet, bit for bit. */
 ilu_status ilu_batch_smooth(ilu_batch bt, void *const *x, const void *const *b, int sweeps, void *stream);
 
 /* ----------------------------------------------------------- request loop -- */

@@ -280,3 +280,34 @@ class Tet:
         out = np.zeros(15)
         _check(lib().ilu_stencil(self.h, int(x), int(y), int(z), _ptr(out)))
         return out
+
+
+class Batch:
+    """Tets smoothed together (wraps an ilu_batch handle).  Keeps the Tet
+    objects alive for as long as the batch exists."""
+
+    def __init__(self, tets, slabs=0, max_wait_spins=0):
+        self.tets = list(tets)
+        arr = (ctypes.c_void_p * len(self.tets))(*[t.h.value for t in self.tets])
+        o = make_opts(slabs=slabs, max_wait_spins=max_wait_spins)
+        h = ctypes.c_void_p()
+        _check(lib().ilu_batch_create(arr, len(self.tets), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ilu_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def smooth(self, xs, bs, sweeps=1, stream=None):
+        n = len(self.tets)
+        assert len(xs) == n and len(bs) == n
+        xa = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in xs])
+        ba = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in bs])
+        _check(lib().ilu_batch_smooth(self.h, xa, ba, int(sweeps), _stream(stream)))

@@ -1,0 +1,379 @@
+// batch.cu -- many macro-tetrahedra smoothed together (ilu_batch_*).
+//
+// A pass over the batch (one sweep of Alg. 2 on every tet) is
+//   1. one reset of all progress words and ticket counters,
+//   2. one residual launch covering every tet (1-D grid, per-tet block ranges),
+//   3. per group of tets with the same level and row-polynomial layout, one
+//      forward and one backward wavefront launch; the groups are independent
+//      branches of the pass, so their kernels run concurrently.
+// Inside a group the clusters of every tet take tickets tet by tet, in
+// dependency order within a tet, so any cluster waits only on clusters that
+// took earlier tickets and are therefore resident or finished: the launch
+// cannot deadlock whatever the residency.  A tet whose row degree is below
+// its group's register degree evaluates zero leading coefficients, which
+// leaves its results bit for bit those of its own launch.
+//
+// The passes of one ilu_batch_smooth call are captured once into a CUDA graph
+// (re-captured when `sweeps` changes) and replayed on the caller's stream.
+// The batch reuses each tet's scratch vector and tables: a tet must not be
+// smoothed through its own handle or another batch while a batch call on it
+// runs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ilu.h"
+#include "kernels.cuh"
+
+using namespace ilu;
+
+namespace ilu {
+void set_last_error(const std::string &msg);
+}
+
+namespace {
+
+ilu_status fail(ilu_status s, const std::string &msg) {
+  set_last_error(msg);
+  return s;
+}
+
+#define BK(call, what)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(ILU_ECUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr long long kBatchSpins = 4000000;
+
+struct Group {
+  int N = 0, reg = -1, dxp = 0;
+  std::vector<int> members;  // tet indices, in ticket order
+  WaveLaunch wl = {};
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+}  // namespace
+
+struct ilu_batch_s {
+  int device = 0, precision = 0, kind = 0, n = 0;
+  long long max_spins = kBatchSpins;
+  bool failed = false;
+  std::vector<ilu_tet> tets;
+  std::vector<TetView> views;
+  std::vector<DevTet> dev;  // host copies of d_tets
+  std::vector<Group> groups;
+  int total_blocks = 0, nflags = 0;
+  DevTet *d_tets = nullptr;
+  int *d_bprefix = nullptr, *d_maps = nullptr, *d_flags = nullptr;
+  void **d_ptrs = nullptr;  // xs[n] then bs[n]
+  void **h_ptrs = nullptr;  // pinned staging of the pointer arrays
+  cudaEvent_t ptr_ev = nullptr, fork = nullptr;
+  LaunchStatus *d_status = nullptr, *h_status = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_sweeps = 0;
+};
+
+namespace {
+
+void release(ilu_batch b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &g : b->groups) {
+    if (g.st) cudaStreamDestroy(g.st);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ptr_ev) cudaEventDestroy(b->ptr_ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  cudaFree(b->d_tets);
+  cudaFree(b->d_bprefix);
+  cudaFree(b->d_maps);
+  cudaFree(b->d_flags);
+  cudaFree(b->d_ptrs);
+  cudaFree(b->d_status);
+  if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+  if (b->h_status) cudaFreeHost(b->h_status);
+  delete b;
+}
+
+// Build groups, per-tet geometry and flag layout, device arrays and the
+// launch shapes (cluster size: the most resident CTAs, larger clusters on ties).
+ilu_status build(ilu_batch b, int requested_slabs) {
+  const int n = b->n;
+  // groups keyed by (level, register degree class, padded row length)
+  std::map<std::tuple<int, int, int>, int> key;
+  for (int i = 0; i < n; ++i) {
+    const TetView &v = b->views[i];
+    const bool reg = wave_uses_registers(v.kind, v.dx);
+    const auto k = std::make_tuple(-v.N, reg ? 1 : 0, v.rstride);  // largest levels first
+    auto it = key.find(k);
+    if (it == key.end()) {
+      it = key.emplace(k, 0).first;
+    }
+    (void)it;
+  }
+  int gi = 0;
+  for (auto &kv : key) kv.second = gi++;
+  b->groups.assign(key.size(), Group{});
+  for (int i = 0; i < n; ++i) {
+    const TetView &v = b->views[i];
+    const bool reg = wave_uses_registers(v.kind, v.dx);
+    Group &g = b->groups[key[std::make_tuple(-v.N, reg ? 1 : 0, v.rstride)]];
+    g.N = v.N;
+    g.dxp = v.rstride;
+    g.reg = reg ? std::max(g.reg, v.dx) : -1;
+    g.members.push_back(i);
+  }
+  // per-tet descriptors with geometry and progress words in the batch's flag array
+  b->dev.resize(n);
+  int off = 0;
+  for (auto &g : b->groups) {
+    for (int i : g.members) {
+      const TetView &v = b->views[i];
+      DevTet d = *v.dev;
+      d.fwd = wave_geom(v.N, v.kind, v.rstride, v.dx, true, requested_slabs);
+      d.bwd = wave_geom(v.N, v.kind, v.rstride, v.dx, false, requested_slabs);
+      d.fwd.prog = off;
+      d.bwd.prog = off + d.fwd.P;
+      off += d.fwd.P + d.bwd.P;
+      d.fwd.ticket = d.bwd.ticket = -1;  // batch launches count tickets in the group's counters
+      b->dev[i] = d;
+    }
+  }
+  const int ticket0 = off;
+  b->nflags = off + 2 * (int)b->groups.size();
+  // residual block ranges
+  std::vector<int> bprefix(n + 1, 0);
+  for (int i = 0; i < n; ++i) bprefix[i + 1] = bprefix[i] + residual_blocks(b->views[i].N);
+  b->total_blocks = bprefix[n];
+  BK(cudaMalloc(&b->d_flags, sizeof(int) * b->nflags), "cudaMalloc flags");
+  BK(cudaMemset(b->d_flags, 0, sizeof(int) * b->nflags), "cudaMemset flags");
+  for (auto &d : b->dev) d.flags = b->d_flags;
+  BK(cudaMalloc(&b->d_tets, sizeof(DevTet) * n), "cudaMalloc tets");
+  BK(cudaMemcpy(b->d_tets, b->dev.data(), sizeof(DevTet) * n, cudaMemcpyHostToDevice), "upload tets");
+  BK(cudaMalloc(&b->d_bprefix, sizeof(int) * (n + 1)), "cudaMalloc block prefix");
+  BK(cudaMemcpy(b->d_bprefix, bprefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "upload prefix");
+  BK(cudaMalloc(&b->d_ptrs, sizeof(void *) * 2 * n), "cudaMalloc pointer arrays");
+  BK(cudaMemset(b->d_ptrs, 0, sizeof(void *) * 2 * n), "cudaMemset pointer arrays");
+  BK(cudaMallocHost(&b->h_ptrs, sizeof(void *) * 2 * n), "cudaMallocHost pointer arrays");
+  BK(cudaMalloc(&b->d_status, sizeof(LaunchStatus)), "cudaMalloc status");
+  BK(cudaMemset(b->d_status, 0, sizeof(LaunchStatus)), "cudaMemset status");
+  BK(cudaMallocHost(&b->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
+  std::memset(b->h_status, 0, sizeof(LaunchStatus));
+  // cluster maps: per group prefix_f (m+1), prefix_b (m+1), order (m)
+  std::vector<int> maps;
+  std::vector<size_t> map_at(b->groups.size());
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    Group &G = b->groups[g];
+    WaveLaunch &L = G.wl;
+    L = {};
+    L.tets = b->d_tets;
+    L.kind = b->kind;
+    L.reg = G.reg;
+    L.dxp = G.dxp;
+    for (int i : G.members) {
+      const DevTet &d = b->dev[i];
+      const TetView &v = b->views[i];
+      L.block_f = std::max(L.block_f, (d.fwd.zb * d.fwd.wpl + 1) * 32);
+      L.block_b = std::max(L.block_b, (d.bwd.zb * d.bwd.wpl + 1) * 32);
+      L.smem_f = std::max(L.smem_f, wave_smem_bytes(v.N, d.fwd, b->kind, v.rstride, G.reg < 0 ? 99 : G.reg, true));
+      L.smem_b = std::max(L.smem_b, wave_smem_bytes(v.N, d.bwd, b->kind, v.rstride, G.reg < 0 ? 99 : G.reg, false));
+      L.maxP_f = std::max(L.maxP_f, d.fwd.P);
+      L.maxP_b = std::max(L.maxP_b, d.bwd.P);
+    }
+    int qf[1 + kClusterCands] = {}, qb[1 + kClusterCands] = {};
+    BK(launch_forward(L, nullptr, 0, nullptr, qf), "cluster query");
+    BK(launch_backward(L, nullptr, 0, nullptr, qb), "cluster query");
+    auto best = [](const int *q, int maxP) {
+      int cs = 1, res = 0;
+      for (int i = 0; i < kClusterCands; ++i) {
+        const int c = std::min(kClusterSizes[i], maxP);
+        if (q[1 + i] * c > res) {
+          res = q[1 + i] * c;
+          cs = c;
+        }
+      }
+      return cs;
+    };
+    L.csize_f = best(qf, L.maxP_f);
+    L.csize_b = best(qb, L.maxP_b);
+    const size_t m = G.members.size();
+    map_at[g] = maps.size();
+    maps.push_back(0);
+    for (int i : G.members) maps.push_back(maps.back() + (b->dev[i].fwd.P + L.csize_f - 1) / L.csize_f);
+    L.clusters_f = maps.back();
+    maps.push_back(0);
+    for (int i : G.members) maps.push_back(maps.back() + (b->dev[i].bwd.P + L.csize_b - 1) / L.csize_b);
+    L.clusters_b = maps.back();
+    for (int i : G.members) maps.push_back(i);
+    (void)m;
+  }
+  BK(cudaMalloc(&b->d_maps, sizeof(int) * maps.size()), "cudaMalloc cluster maps");
+  BK(cudaMemcpy(b->d_maps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice), "upload cluster maps");
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    Group &G = b->groups[g];
+    const int m = (int)G.members.size();
+    const int *pf = b->d_maps + map_at[g], *pb = pf + m + 1, *order = pb + m + 1;
+    G.wl.map_f = {pf, order, m, b->d_flags + ticket0 + 2 * (int)g, nullptr, nullptr};
+    G.wl.map_b = {pb, order, m, b->d_flags + ticket0 + 2 * (int)g + 1, b->d_ptrs, nullptr};
+    BK(cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking), "cudaStreamCreate");
+    BK(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming), "cudaEventCreate");
+  }
+  BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "cudaStreamCreate");
+  BK(cudaEventCreateWithFlags(&b->ptr_ev, cudaEventDisableTiming), "cudaEventCreate");
+  BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "cudaEventCreate");
+  return ILU_OK;
+}
+
+// record `sweeps` passes on the capture stream (the groups fork and join)
+ilu_status record_passes(ilu_batch b, int sweeps) {
+  cudaStream_t s = b->cap;
+  for (int k = 0; k < sweeps; ++k) {
+    BK(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * b->nflags, s), "reset flags");
+    BK(launch_residual_batch(b->d_tets, b->d_bprefix, b->n, b->total_blocks, b->kind, b->d_ptrs,
+                             b->d_ptrs + b->n, s),
+       "batched residual launch");
+    BK(cudaEventRecord(b->fork, s), "fork");
+    for (auto &g : b->groups) {
+      BK(cudaStreamWaitEvent(g.st, b->fork, 0), "fork wait");
+      BK(launch_forward(g.wl, b->d_status, b->max_spins, g.st), "forward launch");
+      BK(launch_backward(g.wl, b->d_status, b->max_spins, g.st), "backward launch");
+      BK(cudaEventRecord(g.done, g.st), "join");
+      BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
+    }
+  }
+  return ILU_OK;
+}
+
+ilu_status capture(ilu_batch b, int sweeps) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed), "begin capture");
+  ilu_status st = record_passes(b, sweeps);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+  if (st != ILU_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(ILU_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return fail(ILU_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  b->graph_sweeps = sweeps;
+  return ILU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, ilu_batch *out) {
+  if (!out) return fail(ILU_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!tets || n <= 0) return fail(ILU_EINVAL, "empty batch");
+  ilu_batch b = new (std::nothrow) ilu_batch_s;
+  if (!b) return fail(ILU_ENOMEM, "out of host memory");
+  b->n = n;
+  b->tets.assign(tets, tets + n);
+  b->views.resize(n);
+  for (int i = 0; i < n; ++i) {
+    if (!tet_view(tets[i], &b->views[i])) {
+      delete b;
+      return fail(ILU_EINVAL, "tet " + std::to_string(i) + " is null or has no device part");
+    }
+    const TetView &v = b->views[i];
+    if (v.failed) {
+      delete b;
+      return fail(ILU_EINVAL, "tet " + std::to_string(i) + " failed earlier");
+    }
+    if (v.device != b->views[0].device || v.precision != b->views[0].precision) {
+      delete b;
+      return fail(ILU_EINVAL, "the tets of a batch share one device and one precision");
+    }
+  }
+  b->device = b->views[0].device;
+  b->precision = b->views[0].precision;
+  b->kind = b->views[0].kind;
+  if (opts && opts->max_wait_spins > 0) b->max_spins = opts->max_wait_spins;
+  if (cudaSetDevice(b->device) != cudaSuccess) {
+    delete b;
+    return fail(ILU_ECUDA, "cudaSetDevice");
+  }
+  ilu_status st = build(b, opts ? opts->slabs : 0);
+  if (st != ILU_OK) {
+    const std::string msg = ilu_last_error();
+    release(b);
+    return fail(st, msg);
+  }
+  *out = b;
+  return ILU_OK;
+}
+
+ilu_status ilu_batch_destroy(ilu_batch b) {
+  if (!b) return ILU_OK;
+  release(b);
+  return ILU_OK;
+}
+
+ilu_status ilu_batch_smooth(ilu_batch b, void *const *x, const void *const *bv, int sweeps, void *stream) {
+  if (!b || !x || !bv) return fail(ILU_EINVAL, "null argument");
+  if (b->failed) return fail(ILU_ECUDA, "batch failed earlier; destroy it");
+  if (sweeps < 0) return fail(ILU_EINVAL, "negative sweep count");
+  if (sweeps == 0) return ILU_OK;
+  for (int i = 0; i < b->n; ++i)
+    if (!x[i] || !bv[i]) return fail(ILU_EINVAL, "null vector for tet " + std::to_string(i));
+  BK(cudaSetDevice(b->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the staging buffer is reused once the previous pointer upload has run
+  BK(cudaEventSynchronize(b->ptr_ev), "pointer upload");
+  for (int i = 0; i < b->n; ++i) {
+    b->h_ptrs[i] = x[i];
+    b->h_ptrs[b->n + i] = const_cast<void *>(bv[i]);
+  }
+  BK(cudaMemcpyAsync(b->d_ptrs, b->h_ptrs, sizeof(void *) * 2 * b->n, cudaMemcpyHostToDevice, st),
+     "pointer upload");
+  BK(cudaEventRecord(b->ptr_ev, st), "pointer upload");
+  if (!b->exec || b->graph_sweeps != sweeps) {
+    ilu_status s = capture(b, sweeps);
+    if (s != ILU_OK) {
+      b->failed = true;
+      return s;
+    }
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, st);
+  if (e != cudaSuccess) {
+    b->failed = true;
+    return fail(ILU_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(b->h_status, b->d_status, sizeof(LaunchStatus), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    b->failed = true;
+    return fail(ILU_ECUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+  }
+  if (b->h_status->code != 0) {
+    b->failed = true;
+    return fail(ILU_ETIMEOUT, "a bounded device wait ran out in the batch (slab " +
+                                  std::to_string(b->h_status->where) + ", level " +
+                                  std::to_string(b->h_status->level) + ")");
+  }
+  return ILU_OK;
+}
+
+}  // extern "C"

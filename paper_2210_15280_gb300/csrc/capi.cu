@@ -55,6 +55,9 @@ struct ilu_tet_s {
   void *d_tabF = nullptr, *d_tabB = nullptr, *d_w = nullptr;
   double *d_kappa = nullptr, *d_partials = nullptr, *d_norms = nullptr;
   int *d_flags = nullptr;
+  DevTet *d_dev = nullptr;  // device copy of dev
+  int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
+  WaveLaunch wl = {};       // the forward/backward launch shape of this tet
   LaunchStatus *d_status = nullptr, *h_status = nullptr;
   int nblocks = 0, norms_cap = 0;
   void *d_xs = nullptr, *d_bs = nullptr;  // staging for ilu_smooth_host
@@ -87,6 +90,8 @@ void free_device(ilu_tet t) {
   t->ev_pool.clear();
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa);
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
+  cudaFree(t->d_dev); cudaFree(t->d_map);
+  t->d_dev = nullptr; t->d_map = nullptr;
   cudaFree(t->d_xs); cudaFree(t->d_bs);
   cudaFree(t->d_r); cudaFree(t->d_z); cudaFree(t->d_p); cudaFree(t->d_q); cudaFree(t->d_zero);
   cudaFree(t->d_dot); cudaFree(t->d_scal);
@@ -115,7 +120,7 @@ WaveGeom pick_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
   zb = std::min(zb, layers);
   while (zb > 1) {
     g.zb = zb;
-    if (wave_smem_bytes(N, g, kind, dxp, fwd) <= 200 * 1024) break;
+    if (wave_smem_bytes(N, g, kind, dxp, dx, fwd) <= 200 * 1024) break;
     --zb;
   }
   g.zb = zb;
@@ -135,17 +140,40 @@ void choose_geometry(ilu_tet t, int requested) {
   t->nflags = d.fwd.P + d.bwd.P + 2;
 }
 
-// largest schedulable cluster per substitution kernel (one cluster holds the
-// whole tet when it has at most that many slabs)
+// Launch shape of one tet's substitutions; cluster sizes from the device's
+// limit for that shape (one cluster holds the whole tet when it has at most
+// that many slabs), then the device copies of the tet and its cluster map.
 ilu_status choose_clusters(ilu_tet t) {
   DevTet &d = t->dev;
-  int cf = 1, cb = 1;
-  d.fwd.csize = d.bwd.csize = 1;
-  CK(launch_forward(d, t->kind(), nullptr, 0, nullptr, &cf), "cluster query");
-  CK(launch_backward(d, t->kind(), nullptr, nullptr, 0, nullptr, &cb), "cluster query");
+  const HostTet &h = t->host;
+  WaveLaunch &L = t->wl;
+  L = {};
+  L.tets = t->d_dev;
+  L.kind = t->kind();
+  L.reg = wave_uses_registers(L.kind, h.dx) ? h.dx : -1;
+  L.dxp = h.rstride;
+  L.block_f = (d.fwd.zb * d.fwd.wpl + 1) * 32;
+  L.block_b = (d.bwd.zb * d.bwd.wpl + 1) * 32;
+  L.smem_f = wave_smem_bytes(h.N, d.fwd, L.kind, h.rstride, h.dx, true);
+  L.smem_b = wave_smem_bytes(h.N, d.bwd, L.kind, h.rstride, h.dx, false);
+  L.maxP_f = d.fwd.P;
+  L.maxP_b = d.bwd.P;
+  int qf[1 + kClusterCands] = {}, qb[1 + kClusterCands] = {};
+  CK(launch_forward(L, nullptr, 0, nullptr, qf), "cluster query");
+  CK(launch_backward(L, nullptr, 0, nullptr, qb), "cluster query");
+  const int cf = qf[0], cb = qb[0];
   // as few clusters as the limit allows, as evenly filled as possible
   d.fwd.csize = (d.fwd.P + (d.fwd.P + cf - 1) / cf - 1) / ((d.fwd.P + cf - 1) / cf);
   d.bwd.csize = (d.bwd.P + (d.bwd.P + cb - 1) / cb - 1) / ((d.bwd.P + cb - 1) / cb);
+  L.csize_f = d.fwd.csize;
+  L.csize_b = d.bwd.csize;
+  L.clusters_f = (d.fwd.P + L.csize_f - 1) / L.csize_f;
+  L.clusters_b = (d.bwd.P + L.csize_b - 1) / L.csize_b;
+  const int map[5] = {0, L.clusters_f, 0, L.clusters_b, 0};
+  CK(cudaMemcpy(t->d_map, map, sizeof(map), cudaMemcpyHostToDevice), "upload cluster map");
+  CK(cudaMemcpy(t->d_dev, &d, sizeof(DevTet), cudaMemcpyHostToDevice), "upload tet");
+  L.map_f = {t->d_map, t->d_map + 4, 1, t->d_flags + d.fwd.ticket, nullptr, nullptr};
+  L.map_b = {t->d_map + 2, t->d_map + 4, 1, t->d_flags + d.bwd.ticket, nullptr, nullptr};
   return ILU_OK;
 }
 
@@ -173,6 +201,8 @@ ilu_status upload(ilu_tet t) {
   CK(cudaMalloc(&t->d_status, sizeof(LaunchStatus)), "cudaMalloc status");
   CK(cudaMemset(t->d_status, 0, sizeof(LaunchStatus)), "cudaMemset status");
   CK(cudaMallocHost(&t->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
+  CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
+  CK(cudaMalloc(&t->d_map, sizeof(int) * 5), "cudaMalloc cluster map");
   std::memset(t->h_status, 0, sizeof(LaunchStatus));
   t->nblocks = std::max(1, residual_blocks(h.N));
   CK(cudaMalloc(&t->d_partials, sizeof(double) * t->nblocks), "cudaMalloc partials");
@@ -291,11 +321,13 @@ ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStre
   }
   {
     Traced tr(t, 1, st);
-    CK(launch_forward(t->dev, t->kind(), t->d_status, t->max_spins, st), "forward launch");
+    CK(launch_forward(t->wl, t->d_status, t->max_spins, st), "forward launch");
   }
   {
     Traced tr(t, 2, st);
-    CK(launch_backward(t->dev, t->kind(), x, t->d_status, t->max_spins, st), "backward launch");
+    WaveLaunch L = t->wl;
+    L.map_b.x0 = x;
+    CK(launch_backward(L, t->d_status, t->max_spins, st), "backward launch");
   }
   return ILU_OK;
 }
@@ -310,11 +342,13 @@ ilu_status precond(ilu_tet t, const void *r, void *z, cudaStream_t st) {
   CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
   {
     Traced tr(t, 1, st);
-    CK(launch_forward(t->dev, t->kind(), t->d_status, t->max_spins, st), "forward launch");
+    CK(launch_forward(t->wl, t->d_status, t->max_spins, st), "forward launch");
   }
   {
     Traced tr(t, 2, st);
-    CK(launch_backward(t->dev, t->kind(), z, t->d_status, t->max_spins, st), "backward launch");
+    WaveLaunch L = t->wl;
+    L.map_b.x0 = z;
+    CK(launch_backward(L, t->d_status, t->max_spins, st), "backward launch");
   }
   return ILU_OK;
 }
@@ -352,6 +386,22 @@ const DevTet *tet_dev_view(ilu_tet t, int *device, int *precision, size_t *nnode
   return t->device >= 0 ? &t->dev : nullptr;
 }
 void set_last_error(const std::string &msg) { g_err = msg; }
+bool tet_view(ilu_tet t, TetView *v) {
+  if (!t || t->device < 0) return false;
+  v->dev = &t->dev;
+  v->N = t->host.N;
+  v->dx = t->host.dx;
+  v->rstride = t->host.rstride;
+  v->device = t->device;
+  v->precision = t->precision;
+  v->kind = t->kind();
+  v->nnodes = t->nnodes();
+  v->failed = t->failed;
+  return true;
+}
+WaveGeom wave_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
+  return pick_geom(N, kind, dxp, dx, fwd, requested);
+}
 }  // namespace ilu
 
 extern "C" {

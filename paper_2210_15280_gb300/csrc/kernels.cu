@@ -38,80 +38,87 @@ __device__ __forceinline__ void star_all(std::integer_sequence<int, E...>, doubl
 
 // --------------------------------------------------------------- residual --
 
-// r = b - A x at interior points of rows (y, z); one warp per row.
+// r = b - A x at the interior points of row (y, z), one warp; returns this
+// lane's share of ||r||^2.  A15/Wstar/kappa come from t (kernel parameter or
+// device memory).
+template <typename TX, typename TR, typename TW, bool VAR>
+__device__ __forceinline__ double residual_row(const DevTet &t, int N, int y, int z, int lane,
+                                               const TX *__restrict__ x, const TX *__restrict__ b,
+                                               TW *__restrict__ r) {
+  double acc2 = 0.0;
+  if (y + z > N - 2) return acc2;
+  const int n = N - 1 - y - z;
+  // row starts of the seven rows the stencil touches
+  const int64_t r0 = grid_index(N, 0, y, z);          // (y, z)
+  const int64_t rs = grid_index(N, 0, y - 1, z);      // (y-1, z)
+  const int64_t rn = grid_index(N, 0, y + 1, z);      // (y+1, z)
+  const int64_t rb = grid_index(N, 0, y, z - 1);      // (y, z-1)
+  const int64_t rbn = grid_index(N, 0, y + 1, z - 1); // (y+1, z-1)
+  const int64_t rt = grid_index(N, 0, y, z + 1);      // (y, z+1)
+  const int64_t rts = grid_index(N, 0, y - 1, z + 1); // (y-1, z+1)
+  for (int xx = 1 + lane; xx <= n; xx += 32) {
+    // neighbour values in the order of D: w s se bnw bn bc be c e n nw tse ts tc tw
+    TR xv[15];
+    xv[0] = (TR)x[r0 + xx - 1];
+    xv[1] = (TR)x[rs + xx];
+    xv[2] = (TR)x[rs + xx + 1];
+    xv[3] = (TR)x[rbn + xx - 1];
+    xv[4] = (TR)x[rbn + xx];
+    xv[5] = (TR)x[rb + xx];
+    xv[6] = (TR)x[rb + xx + 1];
+    xv[7] = (TR)x[r0 + xx];
+    xv[8] = (TR)x[r0 + xx + 1];
+    xv[9] = (TR)x[rn + xx];
+    xv[10] = (TR)x[rn + xx - 1];
+    xv[11] = (TR)x[rts + xx + 1];
+    xv[12] = (TR)x[rts + xx];
+    xv[13] = (TR)x[rt + xx];
+    xv[14] = (TR)x[rt + xx - 1];
+    TR res = (TR)b[r0 + xx];
+    if (!VAR) {
+#pragma unroll
+      for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
+    } else {
+      const double *kap = t.kappa;
+      double kq[15];
+      kq[0] = kap[r0 + xx - 1];
+      kq[1] = kap[rs + xx];
+      kq[2] = kap[rs + xx + 1];
+      kq[3] = kap[rbn + xx - 1];
+      kq[4] = kap[rbn + xx];
+      kq[5] = kap[rb + xx];
+      kq[6] = kap[rb + xx + 1];
+      kq[7] = kap[r0 + xx];
+      kq[8] = kap[r0 + xx + 1];
+      kq[9] = kap[rn + xx];
+      kq[10] = kap[rn + xx - 1];
+      kq[11] = kap[rts + xx + 1];
+      kq[12] = kap[rts + xx];
+      kq[13] = kap[rt + xx];
+      kq[14] = kap[rt + xx - 1];
+      double A[15];
+#pragma unroll
+      for (int d = 0; d < 15; ++d) A[d] = 0.0;
+      star_all(std::make_integer_sequence<int, 100>{}, A, kq, t.Wstar);
+      // rows sum to zero: (A x)_p = sum_{d != c} A_d (x_{p+d} - x_p)
+      const double xc = (double)xv[7];
+#pragma unroll
+      for (int d = 0; d < 15; ++d)
+        if (d != 7) res = (TR)fma(-A[d], (double)xv[d] - xc, (double)res);
+    }
+    r[r0 + xx] = (TW)res;
+    acc2 += (double)res * (double)res;
+  }
+  return acc2;
+}
+
+// One tet: grid ((N-3+7)/8, N-3), one warp per row, per-block partial norms.
 template <typename TX, typename TR, typename TW, bool VAR>
 __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__restrict__ x,
                                                        const TX *__restrict__ b, TW *__restrict__ r,
                                                        double *__restrict__ partials) {
-  const int N = t.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = blockIdx.y + 1;
-  const int y = blockIdx.x * 8 + warp + 1;
-  double acc2 = 0.0;
-  if (y + z <= N - 2) {
-    const int n = N - 1 - y - z;
-    // row starts of the seven rows the stencil touches
-    const int64_t r0 = grid_index(N, 0, y, z);          // (y, z)
-    const int64_t rs = grid_index(N, 0, y - 1, z);      // (y-1, z)
-    const int64_t rn = grid_index(N, 0, y + 1, z);      // (y+1, z)
-    const int64_t rb = grid_index(N, 0, y, z - 1);      // (y, z-1)
-    const int64_t rbn = grid_index(N, 0, y + 1, z - 1); // (y+1, z-1)
-    const int64_t rt = grid_index(N, 0, y, z + 1);      // (y, z+1)
-    const int64_t rts = grid_index(N, 0, y - 1, z + 1); // (y-1, z+1)
-    for (int xx = 1 + lane; xx <= n; xx += 32) {
-      // neighbour values in the order of D: w s se bnw bn bc be c e n nw tse ts tc tw
-      TR xv[15];
-      xv[0] = (TR)x[r0 + xx - 1];
-      xv[1] = (TR)x[rs + xx];
-      xv[2] = (TR)x[rs + xx + 1];
-      xv[3] = (TR)x[rbn + xx - 1];
-      xv[4] = (TR)x[rbn + xx];
-      xv[5] = (TR)x[rb + xx];
-      xv[6] = (TR)x[rb + xx + 1];
-      xv[7] = (TR)x[r0 + xx];
-      xv[8] = (TR)x[r0 + xx + 1];
-      xv[9] = (TR)x[rn + xx];
-      xv[10] = (TR)x[rn + xx - 1];
-      xv[11] = (TR)x[rts + xx + 1];
-      xv[12] = (TR)x[rts + xx];
-      xv[13] = (TR)x[rt + xx];
-      xv[14] = (TR)x[rt + xx - 1];
-      TR res = (TR)b[r0 + xx];
-      if (!VAR) {
-#pragma unroll
-        for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
-      } else {
-        const double *kap = t.kappa;
-        double kq[15];
-        kq[0] = kap[r0 + xx - 1];
-        kq[1] = kap[rs + xx];
-        kq[2] = kap[rs + xx + 1];
-        kq[3] = kap[rbn + xx - 1];
-        kq[4] = kap[rbn + xx];
-        kq[5] = kap[rb + xx];
-        kq[6] = kap[rb + xx + 1];
-        kq[7] = kap[r0 + xx];
-        kq[8] = kap[r0 + xx + 1];
-        kq[9] = kap[rn + xx];
-        kq[10] = kap[rn + xx - 1];
-        kq[11] = kap[rts + xx + 1];
-        kq[12] = kap[rts + xx];
-        kq[13] = kap[rt + xx];
-        kq[14] = kap[rt + xx - 1];
-        double A[15];
-#pragma unroll
-        for (int d = 0; d < 15; ++d) A[d] = 0.0;
-        star_all(std::make_integer_sequence<int, 100>{}, A, kq, t.Wstar);
-        // rows sum to zero: (A x)_p = sum_{d != c} A_d (x_{p+d} - x_p)
-        const double xc = (double)xv[7];
-#pragma unroll
-        for (int d = 0; d < 15; ++d)
-          if (d != 7) res = (TR)fma(-A[d], (double)xv[d] - xc, (double)res);
-      }
-      r[r0 + xx] = (TW)res;
-      acc2 += (double)res * (double)res;
-    }
-  }
+  double acc2 = residual_row<TX, TR, TW, VAR>(t, t.N, blockIdx.x * 8 + warp + 1, blockIdx.y + 1, lane, x, b, r);
   // deterministic block reduction of the squared norm
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
@@ -123,6 +130,32 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
     for (int k = 0; k < 8; ++k) s += red[k];
     partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// Many tets: 1-D grid, tet i owns blocks [bprefix[i], bprefix[i+1]) laid out
+// as its single-tet grid; the result goes to the tet's scratch w.
+template <typename TX, typename TR, typename TW>
+__global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__restrict__ tets,
+                                                             const int *__restrict__ bprefix, int n,
+                                                             const TX *const *__restrict__ xs,
+                                                             const TX *const *__restrict__ bs) {
+  int lo = 0, hi = n - 1;
+  const int blk = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bprefix[mid] <= blk) lo = mid;
+    else hi = mid - 1;
+  }
+  const DevTet &t = tets[lo];
+  const int N = t.N;
+  const int gx = (N - 3 + 7) / 8, local = blk - bprefix[lo];
+  const int by = local / gx, bx = local - by * gx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  TW *r = reinterpret_cast<TW *>(t.w);
+  if (t.const_kappa)
+    residual_row<TX, TR, TW, false>(t, N, bx * 8 + warp + 1, by + 1, lane, xs[lo], bs[lo], r);
+  else
+    residual_row<TX, TR, TW, true>(t, N, bx * 8 + warp + 1, by + 1, lane, xs[lo], bs[lo], r);
 }
 
 // ------------------------------------------------- solver vector helpers --
@@ -252,6 +285,21 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
       residual_kernel<float, float, float, false><<<grid, 256, 0, st>>>(t, (const float *)x, (const float *)b,
                                                                           (float *)r_out, partials);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n, int total_blocks, int kind,
+                                  const void *const *xs, const void *const *bs, cudaStream_t st) {
+  if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+  if (kind == kSweepF64)
+    residual_batch_kernel<double, double, double><<<total_blocks, 256, 0, st>>>(
+        tets, bprefix, n, reinterpret_cast<const double *const *>(xs), reinterpret_cast<const double *const *>(bs));
+  else if (kind == kSweepMixed)
+    residual_batch_kernel<double, double, float><<<total_blocks, 256, 0, st>>>(
+        tets, bprefix, n, reinterpret_cast<const double *const *>(xs), reinterpret_cast<const double *const *>(bs));
+  else
+    residual_batch_kernel<float, float, float><<<total_blocks, 256, 0, st>>>(
+        tets, bprefix, n, reinterpret_cast<const float *const *>(xs), reinterpret_cast<const float *const *>(bs));
   return cudaGetLastError();
 }
 

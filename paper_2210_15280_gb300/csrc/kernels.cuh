@@ -7,6 +7,8 @@
 
 #include "grid.h"
 
+struct ilu_tet_s;
+
 namespace ilu {
 
 // Partition of a tet for one substitution: zb face layers per z-slab (CTA),
@@ -48,18 +50,71 @@ enum SweepKind { kSweepF64 = 0, kSweepF32 = 1, kSweepMixed = 2 };
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st);
+// Residual of many tets in one launch: tet i owns blocks [bprefix[i], bprefix[i+1])
+// of the 1-D grid (bprefix[n] = total, residual_blocks(N_i) each); tets and
+// the pointer arrays are device memory.  Writes w of each tet; no norms.
+cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n, int total_blocks, int kind,
+                                  const void *const *xs, const void *const *bs, cudaStream_t st);
 cudaError_t launch_norm_finish(const double *partials, int n, double *out, cudaStream_t st);
-// With cluster_query set nothing is launched: it receives the largest cluster
-// size the device can schedule for this tet's kernel.
-cudaError_t launch_forward(const DevTet &t, int kind, LaunchStatus *status, long long max_spins, cudaStream_t st,
+
+// Clusters of a substitution launch handed out as tickets: tets in `order`,
+// tet order[j] taking tickets [prefix[j], prefix[j+1]) in dependency order.
+// `ticket` is the zeroed counter; the backward launch adds x (per tet in xs,
+// or x0 for every tet).  All pointers are device memory.
+struct BatchMap {
+  const int *prefix;
+  const int *order;
+  int n;
+  int *ticket;
+  void *const *xs;
+  void *x0;
+};
+
+// One substitution launch over one or more tets (same sweep kind and row
+// polynomial layout): block sizes, shared memory and cluster shapes are the
+// maxima over its tets.
+struct WaveLaunch {
+  const DevTet *tets;  // device array
+  int kind;            // SweepKind
+  int reg;             // register path: row degree (0..7), or -1 (rows read from shared memory)
+  int dxp;             // padded coefficients per row function (rstride of the tets)
+  BatchMap map_f, map_b;
+  int block_f, block_b;    // threads per CTA
+  size_t smem_f, smem_b;   // dynamic shared memory per CTA
+  int csize_f, csize_b;    // CTAs per cluster
+  int clusters_f, clusters_b;
+  int maxP_f, maxP_b;      // most slabs of any tet
+};
+
+// Cluster sizes the launchers consider, largest first.
+constexpr int kClusterCands = 6;
+constexpr int kClusterSizes[kClusterCands] = {16, 12, 8, 4, 2, 1};
+// With cluster_query (int[1 + kClusterCands]) set nothing is launched:
+// [0] receives the largest cluster size the device can schedule for the
+// launch's shape, [1 + i] how many clusters of min(kClusterSizes[i], maxP)
+// CTAs can be resident at once (0 if none fit).
+cudaError_t launch_forward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
                            int *cluster_query = nullptr);
-cudaError_t launch_backward(const DevTet &t, int kind, void *x, LaunchStatus *status, long long max_spins,
-                            cudaStream_t st, int *cluster_query = nullptr);
-size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, bool forward);
+cudaError_t launch_backward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
+                            int *cluster_query = nullptr);
+size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool forward);
 // FP32/MIXED sweeps of degree <= 7 keep each row's polynomials in registers
 // (CTAs of at most 16 warps); otherwise they are read from shared memory.
 bool wave_uses_registers(int kind, int dx);
 int residual_blocks(int N);
+
+// ---- host-side views shared by the entry-point files (capi.cu defines them)
+
+// what a batch needs to know of a tet handle
+struct TetView {
+  const DevTet *dev;  // host copy of the device descriptor
+  int N, dx, rstride, device, precision, kind;
+  size_t nnodes;
+  bool failed;
+};
+bool tet_view(ilu_tet_s *t, TetView *v);
+// partition of one substitution (requested > 0: about that many slabs)
+WaveGeom wave_geom(int N, int kind, int dxp, int dx, bool fwd, int requested);
 
 // solver helpers on full-grid vectors (double if f64, else float)
 constexpr int kDotPartials = 512;

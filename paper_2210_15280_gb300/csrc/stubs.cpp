@@ -1,9 +1,6 @@
 // Temporary: entry points not built yet report ILU_EINVAL.
 #include "../../include/ilu.h"
 extern "C" {
-ilu_status ilu_batch_create(const ilu_tet *, int, const ilu_opts *, ilu_batch *) { return ILU_EINVAL; }
-ilu_status ilu_batch_destroy(ilu_batch) { return ILU_OK; }
-ilu_status ilu_batch_smooth(ilu_batch, void *const *, const void *const *, int, void *) { return ILU_EINVAL; }
 ilu_status ilu_server_create(const ilu_server_opts *, ilu_server *) { return ILU_EINVAL; }
 ilu_status ilu_server_submit(ilu_server, const ilu_request *, uint64_t *) { return ILU_EINVAL; }
 ilu_status ilu_server_wait(ilu_server, uint64_t, int, ilu_result *) { return ILU_EINVAL; }

@@ -269,6 +269,16 @@ __device__ __forceinline__ void cl_sync() {
 __host__ __device__ __forceinline__ int cache_rows(int N) { return N / 2 + 12; }
 // y mod RCC for 1 <= y <= N - 2 < 2 RCC
 __device__ __forceinline__ int cache_slot(int y, int RCC) { return y >= RCC ? y - RCC : y; }
+// In the register path a cached row is only needed from its fetch, D levels
+// before its first point, until its owner lane loads it at that point: a
+// ring of kRowRing slots indexed by y mod kRowRing suffices (in either
+// direction a row's slot is next refetched at least 10 levels after the load).
+constexpr int kRowRing = 16;
+template <int REG>
+__device__ __forceinline__ int row_slot(int y, int RCC) {
+  if constexpr (REG >= 0) return y & (kRowRing - 1);
+  else return cache_slot(y, RCC);
+}
 __host__ __device__ __forceinline__ int level_cap(int N) { return N / 2 + 2; }
 
 // bounded spin of one thread until *p >= target (acquire, cluster scope)
@@ -386,26 +396,30 @@ __device__ __forceinline__ bool wait_halo_level(unsigned long long *hbar, int id
   return true;
 }
 
+// Which tet and which of its clusters a ticket belongs to: the largest j with
+// prefix[j] <= ticket (tickets are handed out tet by tet, in bm.order).
+__device__ __forceinline__ int ticket_owner(const BatchMap &bm, int ticket) {
+  int lo = 0, hi = bm.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bm.prefix[mid] <= ticket) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // --------------------------------------------------------------- forward --
 
 // REG >= 0: FP32 path with the row polynomials (degree REG) in registers,
 // each row pinned to one lane for its whole life; REG < 0: polynomials read
 // from the shared row cache at every point.
 template <typename TW, int DXP, int REG>
-__global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(DevTet t, LaunchStatus *status,
-                                                                   long long max_spins) {
+__global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *__restrict__ tets, BatchMap bm,
+                                                                   LaunchStatus *status, long long max_spins) {
   constexpr int NF = 7;
   constexpr bool F32 = sizeof(TW) == 4;
   constexpr int ROW = F32 ? 8 * DXP : NF * DXP;  // elements per cached row
-  const int N = t.N;
-  const int Zb = t.fwd.zb, wpl = t.fwd.wpl, P = t.fwd.P;
-  const int RC = level_cap(N), RCC = cache_rows(N);
-  const int NCW = Zb * wpl, NCT = NCW * 32;
-  extern __shared__ __align__(16) unsigned char smem[];
-  TW *ring = reinterpret_cast<TW *>(smem);          // [4][Zb][RC]  w of the last levels
-  TW *rin = ring + 4 * Zb * RC;                     // [IS][Zb][RC] r of the next levels
-  TW *halo = rin + IS * Zb * RC;                    // [HS][RC]     layer z_s - 1
-  TW *coef = align16<TW>(halo + HS * RC);           // [Zb][RCC][ROW]
+  const int NCW = (int)(blockDim.x >> 5) - 1, NCT = NCW * 32;  // compute warps (+ one communication warp)
   __shared__ int s_ticket, s_abort, s_nb, s_done, s_cdone;
   __shared__ __align__(8) unsigned long long hbar[HS];
   const unsigned C = cl_size(), rank = cl_rank();
@@ -417,12 +431,22 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(DevTet t, Laun
     for (int i = 0; i < HS; ++i) mbar_init(&hbar[i], 1);
     mbar_init_fence();
     if (rank == 0) {
-      const int tk = atomicAdd(&t.flags[t.fwd.ticket], 1);
+      const int tk = atomicAdd(bm.ticket, 1);
       for (unsigned r = 0; r < C; ++r) cl_st_int(cl_map(&s_ticket, r), tk);
     }
   }
   cl_sync();
-  const int k = s_ticket * (int)C + (int)rank;
+  const int owner = ticket_owner(bm, s_ticket);
+  const DevTet &t = tets[bm.order[owner]];
+  const int N = t.N;
+  const int Zb = t.fwd.zb, wpl = t.fwd.wpl, P = t.fwd.P;
+  const int RC = level_cap(N), RCC = REG >= 0 ? kRowRing : cache_rows(N);
+  extern __shared__ __align__(16) unsigned char smem[];
+  TW *ring = reinterpret_cast<TW *>(smem);          // [4][Zb][RC]  w of the last levels
+  TW *rin = ring + 4 * Zb * RC;                     // [IS][Zb][RC] r of the next levels
+  TW *halo = rin + IS * Zb * RC;                    // [HS][RC]     layer z_s - 1
+  TW *coef = align16<TW>(halo + HS * RC);           // [Zb][RCC][ROW]
+  const int k = (s_ticket - bm.prefix[owner]) * (int)C + (int)rank;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k < P) {
     const int zs = 1 + k * Zb, ze = min(zs + Zb, N - 2);
@@ -457,7 +481,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(DevTet t, Laun
         const int y = v >> 1;
         if (y > N - 2 - z) return;
         const char *src = reinterpret_cast<const char *>(tab + (size_t)(row0 + y) * ROW);
-        char *dst = reinterpret_cast<char *>(my_coef + (size_t)cache_slot(y, RCC) * ROW);
+        char *dst = reinterpret_cast<char *>(my_coef + (size_t)row_slot<REG>(y, RCC) * ROW);
         constexpr int CH = ROW * (int)sizeof(TW) / 16;
         for (int c = lane; c < CH; c += 32) cp_async<16>(dst + 16 * c, src + 16 * c);
       };
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(DevTet t, Laun
             }
             if (ycur <= yhi) {
               if (!have) {
-                regs.template load<DXP>(reinterpret_cast<const float *>(my_coef) + (size_t)cache_slot(ycur, RCC) * ROW);
+                regs.template load<DXP>(reinterpret_cast<const float *>(my_coef) + (size_t)row_slot<REG>(ycur, RCC) * ROW);
                 have = true;
               }
               const int x = s - 2 * ycur - 3 * z;
@@ -613,26 +637,15 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(DevTet t, Laun
 // -------------------------------------------------------------- backward --
 
 template <typename TW, typename TX, int DXP, int REG>
-__global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(DevTet t, TX *__restrict__ xg,
+__global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *__restrict__ tets, BatchMap bm,
                                                                    LaunchStatus *status, long long max_spins) {
   constexpr int NF = 8;
   constexpr bool F32 = sizeof(TW) == 4;
   constexpr int ROW = NF * DXP;  // elements per cached row (FP32: 4 pairs x DXP x 2)
-  const int N = t.N;
-  const int Zb = t.bwd.zb, wpl = t.bwd.wpl, P = t.bwd.P;
-  const int RC = level_cap(N), RCC = cache_rows(N);
-  const int NCW = Zb * wpl, NCT = NCW * 32;
-  const int TOP = 3 * N + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
-  TW *ring = reinterpret_cast<TW *>(smem);       // [4][Zb][RC]
-  TW *win = ring + 4 * Zb * RC;                  // [IS][Zb][RC] forward result of the next levels
-  TW *halo = win + IS * Zb * RC;                 // [HS][RC]     layer z_e
-  TX *xin = align16<TX>(halo + HS * RC);         // [IS][Zb][RC] x of the next levels
-  TW *coef = align16<TW>(xin + IS * Zb * RC);    // [Zb][RCC][ROW]
+  const int NCW = (int)(blockDim.x >> 5) - 1, NCT = NCW * 32;
   __shared__ int s_ticket, s_abort, s_nb, s_done, s_cdone;
   __shared__ __align__(8) unsigned long long hbar[HS];
   const unsigned C = cl_size(), rank = cl_rank();
-  const int Q = (P + (int)C - 1) / (int)C;  // clusters
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_nb = 0;
@@ -641,12 +654,27 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(DevTet t, TX *
     for (int i = 0; i < HS; ++i) mbar_init(&hbar[i], 1);
     mbar_init_fence();
     if (rank == 0) {
-      const int tk = atomicAdd(&t.flags[t.bwd.ticket], 1);
+      const int tk = atomicAdd(bm.ticket, 1);
       for (unsigned r = 0; r < C; ++r) cl_st_int(cl_map(&s_ticket, r), tk);
     }
   }
   cl_sync();
-  const int k = (Q - 1 - s_ticket) * (int)C + (int)rank;  // top clusters first
+  const int owner = ticket_owner(bm, s_ticket);
+  const int ti = bm.order[owner];
+  const DevTet &t = tets[ti];
+  TX *__restrict__ xg = reinterpret_cast<TX *>(bm.xs ? bm.xs[ti] : bm.x0);
+  const int N = t.N;
+  const int Zb = t.bwd.zb, wpl = t.bwd.wpl, P = t.bwd.P;
+  const int RC = level_cap(N), RCC = REG >= 0 ? kRowRing : cache_rows(N);
+  const int TOP = 3 * N + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  TW *ring = reinterpret_cast<TW *>(smem);       // [4][Zb][RC]
+  TW *win = ring + 4 * Zb * RC;                  // [IS][Zb][RC] forward result of the next levels
+  TW *halo = win + IS * Zb * RC;                 // [HS][RC]     layer z_e
+  TX *xin = align16<TX>(halo + HS * RC);         // [IS][Zb][RC] x of the next levels
+  TW *coef = align16<TW>(xin + IS * Zb * RC);    // [Zb][RCC][ROW]
+  const int Q = bm.prefix[owner + 1] - bm.prefix[owner];  // clusters of this tet
+  const int k = (Q - 1 - (s_ticket - bm.prefix[owner])) * (int)C + (int)rank;  // top clusters first
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k < P) {
     const int zs = 1 + k * Zb, ze = min(zs + Zb, N - 2);
@@ -680,7 +708,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(DevTet t, TX *
         const int y = s2 - (N - 1) - 2 * z;
         if (y < 1 || y > N - 2 - z) return;
         const char *src = reinterpret_cast<const char *>(tab + (size_t)(row0 + y) * ROW);
-        char *dst = reinterpret_cast<char *>(my_coef + (size_t)cache_slot(y, RCC) * ROW);
+        char *dst = reinterpret_cast<char *>(my_coef + (size_t)row_slot<REG>(y, RCC) * ROW);
         constexpr int CH = ROW * (int)sizeof(TW) / 16;
         for (int c = lane; c < CH; c += 32) cp_async<16>(dst + 16 * c, src + 16 * c);
       };
@@ -800,7 +828,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(DevTet t, TX *
             }
             if (ycur >= ylo) {
               if (!have) {
-                regs.template load<DXP>(reinterpret_cast<const float *>(my_coef) + (size_t)cache_slot(ycur, RCC) * ROW);
+                regs.template load<DXP>(reinterpret_cast<const float *>(my_coef) + (size_t)row_slot<REG>(ycur, RCC) * ROW);
                 have = true;
               }
               const int x = s - 2 * ycur - 3 * z;
@@ -836,29 +864,30 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(DevTet t, TX *
 }
 
 template <typename TW>
-size_t fwd_smem(int N, const WaveGeom &g, int dxp) {
-  const size_t RC = level_cap(N), RCC = cache_rows(N);
+size_t fwd_smem(int N, const WaveGeom &g, int dxp, bool reg) {
+  const size_t RC = level_cap(N), RCC = reg ? kRowRing : cache_rows(N);
   const size_t nf = sizeof(TW) == 4 ? 8 : 7;
   return sizeof(TW) * ((4 + IS) * g.zb * RC + HS * RC) + 16 + (size_t)g.zb * RCC * nf * dxp * sizeof(TW);
 }
 template <typename TW, typename TX>
-size_t bwd_smem(int N, const WaveGeom &g, int dxp) {
-  const size_t RC = level_cap(N), RCC = cache_rows(N);
+size_t bwd_smem(int N, const WaveGeom &g, int dxp, bool reg) {
+  const size_t RC = level_cap(N), RCC = reg ? kRowRing : cache_rows(N);
   return sizeof(TW) * ((4 + IS) * g.zb * RC + HS * RC) + 16 + sizeof(TX) * IS * g.zb * RC + 16 +
          (size_t)g.zb * RCC * 8 * dxp * sizeof(TW);
 }
 
-// Launch as clusters of g.csize CTAs (slab = cluster ticket * csize + rank).
-// With `query` set, nothing is launched: *query receives the largest cluster
-// size (<= 16, <= P) the device can schedule for this kernel.
-template <typename K, typename... Args>
-cudaError_t cluster_launch(K kernel, const WaveGeom &g, size_t smem, cudaStream_t st, int *query, Args... args) {
+// Launch as clusters of `csize` CTAs covering `clusters` clusters.  With
+// `query` set nothing is launched (see launch_forward).
+template <typename K>
+cudaError_t cluster_launch(K kernel, const WaveLaunch &L, bool fwd, cudaStream_t st, int *query, LaunchStatus *status,
+                           long long max_spins) {
+  const size_t smem = fwd ? L.smem_f : L.smem_b;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(32 * (g.zb * g.wpl + 1));
+  cfg.blockDim = dim3(fwd ? L.block_f : L.block_b);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -868,66 +897,69 @@ cudaError_t cluster_launch(K kernel, const WaveGeom &g, size_t smem, cudaStream_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (query) {
-    const int cands[] = {16, 12, 8, 4, 2, 1};
-    *query = 1;
-    for (int c : cands) {
-      const int cs = c < g.P ? c : g.P;
+    const int maxP = fwd ? L.maxP_f : L.maxP_b;
+    query[0] = 1;
+    bool found = false;
+    for (int i = 0; i < kClusterCands; ++i) {
+      const int cs = kClusterSizes[i] < maxP ? kClusterSizes[i] : maxP;
       attr[0].val.clusterDim.x = cs;
       cfg.gridDim = dim3(cs);
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n > 0) {
-        *query = cs;
-        return cudaSuccess;
+      if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
       }
-      cudaGetLastError();
+      query[1 + i] = n;
+      if (n > 0 && !found) {
+        query[0] = cs;
+        found = true;
+      }
     }
     return cudaSuccess;
   }
-  const int Q = (g.P + g.csize - 1) / g.csize;
-  attr[0].val.clusterDim.x = g.csize;
-  cfg.gridDim = dim3(Q * g.csize);
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
+  const int cs = fwd ? L.csize_f : L.csize_b;
+  attr[0].val.clusterDim.x = cs;
+  cfg.gridDim = dim3((fwd ? L.clusters_f : L.clusters_b) * cs);
+  return cudaLaunchKernelEx(&cfg, kernel, L.tets, fwd ? L.map_f : L.map_b, status, max_spins);
 }
 
 template <typename TW, int DXP, int REG>
-cudaError_t fwd_launch(const DevTet &t, LaunchStatus *status, long long max_spins, cudaStream_t st, int *query) {
-  return cluster_launch(fwd_wave<TW, DXP, REG>, t.fwd, fwd_smem<TW>(t.N, t.fwd, DXP), st, query, t, status,
-                        max_spins);
+cudaError_t fwd_launch(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st, int *query) {
+  return cluster_launch(fwd_wave<TW, DXP, REG>, L, true, st, query, status, max_spins);
 }
 
 template <typename TW, typename TX, int DXP, int REG>
-cudaError_t bwd_launch(const DevTet &t, void *x, LaunchStatus *status, long long max_spins, cudaStream_t st,
-                       int *query) {
-  return cluster_launch(bwd_wave<TW, TX, DXP, REG>, t.bwd, bwd_smem<TW, TX>(t.N, t.bwd, DXP), st, query, t,
-                        (TX *)x, status, max_spins);
+cudaError_t bwd_launch(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st, int *query) {
+  return cluster_launch(bwd_wave<TW, TX, DXP, REG>, L, false, st, query, status, max_spins);
 }
 
-// FP32 dispatch on the row degree: registers for degree <= 7
-cudaError_t fwd32(const DevTet &t, LaunchStatus *s, long long m, cudaStream_t st, int *q) {
-  switch (t.dx) {
-    case 0: return fwd_launch<float, 4, 0>(t, s, m, st, q);
-    case 1: return fwd_launch<float, 4, 1>(t, s, m, st, q);
-    case 2: return fwd_launch<float, 4, 2>(t, s, m, st, q);
-    case 3: return fwd_launch<float, 4, 3>(t, s, m, st, q);
-    case 4: return fwd_launch<float, 8, 4>(t, s, m, st, q);
-    case 5: return fwd_launch<float, 8, 5>(t, s, m, st, q);
-    case 6: return fwd_launch<float, 8, 6>(t, s, m, st, q);
-    case 7: return fwd_launch<float, 8, 7>(t, s, m, st, q);
-    default: return fwd_launch<float, 16, -1>(t, s, m, st, q);
+// FP32 dispatch on the register degree; rows of degree <= 3 are stored with
+// 4 coefficients per function, degree 4..7 with 8
+cudaError_t fwd32(const WaveLaunch &L, LaunchStatus *s, long long m, cudaStream_t st, int *q) {
+  switch (L.reg) {
+    case 0: return fwd_launch<float, 4, 0>(L, s, m, st, q);
+    case 1: return fwd_launch<float, 4, 1>(L, s, m, st, q);
+    case 2: return fwd_launch<float, 4, 2>(L, s, m, st, q);
+    case 3: return fwd_launch<float, 4, 3>(L, s, m, st, q);
+    case 4: return fwd_launch<float, 8, 4>(L, s, m, st, q);
+    case 5: return fwd_launch<float, 8, 5>(L, s, m, st, q);
+    case 6: return fwd_launch<float, 8, 6>(L, s, m, st, q);
+    case 7: return fwd_launch<float, 8, 7>(L, s, m, st, q);
+    default: return fwd_launch<float, 16, -1>(L, s, m, st, q);
   }
 }
 template <typename TX>
-cudaError_t bwd32(const DevTet &t, void *x, LaunchStatus *s, long long m, cudaStream_t st, int *q) {
-  switch (t.dx) {
-    case 0: return bwd_launch<float, TX, 4, 0>(t, x, s, m, st, q);
-    case 1: return bwd_launch<float, TX, 4, 1>(t, x, s, m, st, q);
-    case 2: return bwd_launch<float, TX, 4, 2>(t, x, s, m, st, q);
-    case 3: return bwd_launch<float, TX, 4, 3>(t, x, s, m, st, q);
-    case 4: return bwd_launch<float, TX, 8, 4>(t, x, s, m, st, q);
-    case 5: return bwd_launch<float, TX, 8, 5>(t, x, s, m, st, q);
-    case 6: return bwd_launch<float, TX, 8, 6>(t, x, s, m, st, q);
-    case 7: return bwd_launch<float, TX, 8, 7>(t, x, s, m, st, q);
-    default: return bwd_launch<float, TX, 16, -1>(t, x, s, m, st, q);
+cudaError_t bwd32(const WaveLaunch &L, LaunchStatus *s, long long m, cudaStream_t st, int *q) {
+  switch (L.reg) {
+    case 0: return bwd_launch<float, TX, 4, 0>(L, s, m, st, q);
+    case 1: return bwd_launch<float, TX, 4, 1>(L, s, m, st, q);
+    case 2: return bwd_launch<float, TX, 4, 2>(L, s, m, st, q);
+    case 3: return bwd_launch<float, TX, 4, 3>(L, s, m, st, q);
+    case 4: return bwd_launch<float, TX, 8, 4>(L, s, m, st, q);
+    case 5: return bwd_launch<float, TX, 8, 5>(L, s, m, st, q);
+    case 6: return bwd_launch<float, TX, 8, 6>(L, s, m, st, q);
+    case 7: return bwd_launch<float, TX, 8, 7>(L, s, m, st, q);
+    default: return bwd_launch<float, TX, 16, -1>(L, s, m, st, q);
   }
 }
 
@@ -935,32 +967,33 @@ cudaError_t bwd32(const DevTet &t, void *x, LaunchStatus *s, long long m, cudaSt
 
 bool wave_uses_registers(int kind, int dx) { return kind != kSweepF64 && dx <= 7; }
 
-size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, bool forward) {
-  if (forward) return kind == kSweepF64 ? fwd_smem<double>(N, g, dxp) : fwd_smem<float>(N, g, dxp);
-  if (kind == kSweepF64) return bwd_smem<double, double>(N, g, dxp);
-  if (kind == kSweepMixed) return bwd_smem<float, double>(N, g, dxp);
-  return bwd_smem<float, float>(N, g, dxp);
+size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool forward) {
+  const bool reg = wave_uses_registers(kind, dx);
+  if (forward) return kind == kSweepF64 ? fwd_smem<double>(N, g, dxp, reg) : fwd_smem<float>(N, g, dxp, reg);
+  if (kind == kSweepF64) return bwd_smem<double, double>(N, g, dxp, reg);
+  if (kind == kSweepMixed) return bwd_smem<float, double>(N, g, dxp, reg);
+  return bwd_smem<float, float>(N, g, dxp, reg);
 }
 
-cudaError_t launch_forward(const DevTet &t, int kind, LaunchStatus *status, long long max_spins, cudaStream_t st,
+cudaError_t launch_forward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
                            int *cluster_query) {
-  if (kind == kSweepF64) {
-    if (t.rstride == 4) return fwd_launch<double, 4, -1>(t, status, max_spins, st, cluster_query);
-    if (t.rstride == 8) return fwd_launch<double, 8, -1>(t, status, max_spins, st, cluster_query);
-    return fwd_launch<double, 16, -1>(t, status, max_spins, st, cluster_query);
+  if (L.kind == kSweepF64) {
+    if (L.dxp == 4) return fwd_launch<double, 4, -1>(L, status, max_spins, st, cluster_query);
+    if (L.dxp == 8) return fwd_launch<double, 8, -1>(L, status, max_spins, st, cluster_query);
+    return fwd_launch<double, 16, -1>(L, status, max_spins, st, cluster_query);
   }
-  return fwd32(t, status, max_spins, st, cluster_query);
+  return fwd32(L, status, max_spins, st, cluster_query);
 }
 
-cudaError_t launch_backward(const DevTet &t, int kind, void *x, LaunchStatus *status, long long max_spins,
-                            cudaStream_t st, int *cluster_query) {
-  if (kind == kSweepF64) {
-    if (t.rstride == 4) return bwd_launch<double, double, 4, -1>(t, x, status, max_spins, st, cluster_query);
-    if (t.rstride == 8) return bwd_launch<double, double, 8, -1>(t, x, status, max_spins, st, cluster_query);
-    return bwd_launch<double, double, 16, -1>(t, x, status, max_spins, st, cluster_query);
+cudaError_t launch_backward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
+                            int *cluster_query) {
+  if (L.kind == kSweepF64) {
+    if (L.dxp == 4) return bwd_launch<double, double, 4, -1>(L, status, max_spins, st, cluster_query);
+    if (L.dxp == 8) return bwd_launch<double, double, 8, -1>(L, status, max_spins, st, cluster_query);
+    return bwd_launch<double, double, 16, -1>(L, status, max_spins, st, cluster_query);
   }
-  if (kind == kSweepMixed) return bwd32<double>(t, x, status, max_spins, st, cluster_query);
-  return bwd32<float>(t, x, status, max_spins, st, cluster_query);
+  if (L.kind == kSweepMixed) return bwd32<double>(L, status, max_spins, st, cluster_query);
+  return bwd32<float>(L, status, max_spins, st, cluster_query);
 }
 
 }  // namespace ilu

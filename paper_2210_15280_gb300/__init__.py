@@ -311,3 +311,60 @@ class Batch:
         xa = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in xs])
         ba = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in bs])
         _check(lib().ilu_batch_smooth(self.h, xa, ba, int(sweeps), _stream(stream)))
+
+
+class Server:
+    """The request loop (wraps an ilu_server handle): submit interior solves,
+    wait for their results; the loop admits them by free device memory and
+    runs admitted solves concurrently."""
+
+    def __init__(self, budget_bytes=0.0, max_slots=0, device=0, precision=MIXED):
+        o = ServerOpts(float(budget_bytes), int(max_slots), int(device), int(precision))
+        h = ctypes.c_void_p()
+        _check(lib().ilu_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ilu_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, macro_tet, level, b, coeff=None, poly_degree=4, method=RICHARDSON, rtol=1e-8,
+               max_iter=10000, x0=None):
+        r = Request()
+        r.macro_tet[:] = [float(v) for v in np.asarray(macro_tet, dtype=np.float64).reshape(12)]
+        r.level = int(level)
+        r.coeff = coeff if coeff is not None else make_coeff()
+        r.poly_degree, r.method, r.rtol, r.max_iter = int(poly_degree), int(method), float(rtol), int(max_iter)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        if bb.size != num_nodes(level) or (xx is not None and xx.size != num_nodes(level)):
+            raise ValueError("b and x0 must hold num_nodes(level) values")
+        r.b = bb.ctypes.data
+        r.x0 = None if xx is None else xx.ctypes.data
+        tk = ctypes.c_uint64(0)
+        _check(lib().ilu_server_submit(self.h, ctypes.byref(r), ctypes.byref(tk)))  # copies b and x0
+        return tk.value
+
+    def wait(self, ticket, timeout_ms=-1, release=True):
+        """dict(status, iters, rel_res, latency_ms, x); x is a copy (None on failure)."""
+        res = Result()
+        _check(lib().ilu_server_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res)))
+        x = None
+        if res.x:
+            x = np.ctypeslib.as_array(ctypes.cast(res.x, ctypes.POINTER(ctypes.c_double)), shape=(res.n,)).copy()
+        out = dict(status=res.status, iters=res.iters, rel_res=res.rel_res, latency_ms=res.latency_ms, x=x)
+        if release:
+            _check(lib().ilu_server_release(self.h, ctypes.c_uint64(ticket)))
+        return out
+
+    def stats(self):
+        s = Stats()
+        _check(lib().ilu_server_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}

@@ -882,7 +882,22 @@ template <typename K>
 cudaError_t cluster_launch(K kernel, const WaveLaunch &L, bool fwd, cudaStream_t st, int *query, LaunchStatus *status,
                            long long max_spins) {
   const size_t smem = fwd ? L.smem_f : L.smem_b;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // The dynamic shared-memory cap is a property of the kernel, shared by
+  // every thread and launch in the process: raise it to the device's opt-in
+  // limit less the kernel's static shared memory (the same value from every
+  // caller) rather than to this launch's need, which would race with
+  // concurrent launches of other tets.
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int cap = optin - (int)fa.sharedSizeBytes;
+  if (smem > (size_t)cap) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;

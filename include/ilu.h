@@ -78,7 +78,20 @@ typedef struct {
   int slabs;           /* z-slabs (CTAs) per tet in the sweep; <=0: automatic */
   int device;          /* CUDA device ordinal; -1: host-only handle (setup only) */
   long long max_wait_spins; /* bound on device-side spin waits; <=0: default */
+  int kernel;          /* substitution kernels of FP32/MIXED sweeps: an ilu_kernel value */
 } ilu_opts;
+
+/* Substitution kernels of the FP32/MIXED sweeps.  Both run the same
+ * arithmetic (Alg. 2, V2) and agree to rounding; they differ in how the
+ * hyperplane wavefront is mapped onto the GPU:
+ *   ILU_KERNEL_SLAB  a CTA per z-slab advancing one hyperplane per step with
+ *                    block-wide synchronisation (faster up to level 8);
+ *   ILU_KERNEL_BAND  a warp per (layer, 32-row band) advancing one row point
+ *                    per lane and step, synchronised point to point through
+ *                    tagged words (faster from level 9 on).
+ * ILU_KERNEL_AUTO picks by level.  F64 sweeps and degrees above 7 always use
+ * the slab kernels. */
+typedef enum { ILU_KERNEL_AUTO = 0, ILU_KERNEL_SLAB = 1, ILU_KERNEL_BAND = 2 } ilu_kernel;
 
 typedef struct ilu_tet_s *ilu_tet;
 typedef struct ilu_batch_s *ilu_batch;

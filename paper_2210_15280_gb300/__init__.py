@@ -20,6 +20,7 @@ ILU_OK, ILU_EINVAL, ILU_ENOMEM, ILU_ECUDA, ILU_ESINGULAR, ILU_ENOTCONV, ILU_ETIM
 F64, F32, MIXED = 0, 1, 2
 COEFF_CONST, COEFF_SINPROD, COEFF_KAPPA_I = 0, 1, 2
 RICHARDSON, PCG = 0, 1
+KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND = 0, 1, 2
 STATUS_NAMES = ["ILU_OK", "ILU_EINVAL", "ILU_ENOMEM", "ILU_ECUDA", "ILU_ESINGULAR", "ILU_ENOTCONV",
                 "ILU_ETIMEOUT", "ILU_EBUSY", "ILU_ENODEV"]
 
@@ -47,7 +48,7 @@ class Coeff(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("deg", ctypes.c_int * 3), ("sample_level", ctypes.c_int), ("ridge", ctypes.c_double),
                 ("precision", ctypes.c_int), ("slabs", ctypes.c_int), ("device", ctypes.c_int),
-                ("max_wait_spins", ctypes.c_longlong)]
+                ("max_wait_spins", ctypes.c_longlong), ("kernel", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -168,7 +169,8 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, device=0, max_wait_spins=0):
+def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, device=0, max_wait_spins=0,
+              kernel=0):
     o = Opts()
     lib().ilu_opts_default(ctypes.byref(o))
     if deg is not None:
@@ -177,6 +179,7 @@ def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, d
             o.deg[k] = int(d[k])
     o.sample_level, o.ridge, o.precision = int(sample_level), float(ridge), int(precision)
     o.slabs, o.device, o.max_wait_spins = int(slabs), int(device), int(max_wait_spins)
+    o.kernel = int(kernel)
     return o
 
 

@@ -56,6 +56,16 @@ struct ilu_tet_s {
   double *d_kappa = nullptr, *d_partials = nullptr, *d_norms = nullptr;
   int *d_flags = nullptr;
   DevTet *d_dev = nullptr;  // device copy of dev
+  // FP32 band sweeps (band.cu): layout tables, band array, streams
+  bool use_band = false;
+  int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO;
+  int band_Z = 8, band_ntiles = 0, band_ncta = 0;
+  BandInfo *d_binfo = nullptr;
+  int *d_bint = nullptr;  // CTA list, tile list, cluster map {0, ncta, 0}, tile prefix {0, ntiles}, epoch
+  void *d_bw = nullptr;
+  unsigned long long *d_bstreams = nullptr;
+  BandLaunch bl = {};
+  const int *band_tprefix = nullptr;
   int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
   WaveLaunch wl = {};       // the forward/backward launch shape of this tet
   LaunchStatus *d_status = nullptr, *h_status = nullptr;
@@ -92,6 +102,8 @@ void free_device(ilu_tet t) {
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
   cudaFree(t->d_dev); cudaFree(t->d_map);
   t->d_dev = nullptr; t->d_map = nullptr;
+  cudaFree(t->d_binfo); cudaFree(t->d_bint); cudaFree(t->d_bw); cudaFree(t->d_bstreams);
+  t->d_binfo = nullptr; t->d_bint = nullptr; t->d_bw = nullptr; t->d_bstreams = nullptr;
   cudaFree(t->d_xs); cudaFree(t->d_bs);
   cudaFree(t->d_r); cudaFree(t->d_z); cudaFree(t->d_p); cudaFree(t->d_q); cudaFree(t->d_zero);
   cudaFree(t->d_dot); cudaFree(t->d_scal);
@@ -177,6 +189,89 @@ ilu_status choose_clusters(ilu_tet t) {
   return ILU_OK;
 }
 
+// Band layout of the FP32 sweeps: offsets of every band's block, edge
+// stream and (at the top layer of a CTA's stack) stream to the next CTA;
+// the CTA list in dependency order and the residual/update tiles.
+struct BandPlan {
+  std::vector<BandInfo> info;
+  std::vector<int> cta, tiles;
+  int64_t wfloats = 0, swords = 0;
+};
+
+BandPlan make_band_plan(int N, int Z) {
+  BandPlan p;
+  const int KB = band_kmax(N) + 1;
+  p.info.assign((size_t)std::max(N - 3, 0) * KB, BandInfo{-1, -1, -1});
+  for (int z = 1; z <= N - 3; ++z)
+    for (int k = band_kmin(z); k < KB; ++k) {
+      const int shi = band_shi(N, z, k);
+      BandInfo &b = p.info[(size_t)(z - 1) * KB + k];
+      b.off = p.wfloats;
+      p.wfloats += (int64_t)shi * 32;
+      b.hoff = p.swords;  // 16-byte records 0 .. shi + 127
+      p.swords += 2 * ((int64_t)shi + 128);
+      if (z % Z == 0 && band_exists(N, z + 1, k)) {
+        b.voff = p.swords;  // [step 0 .. shi][32]
+        p.swords += ((int64_t)shi + 2) * 32;
+      }
+      for (int ch = 0; ch < (shi + 31) / 32; ++ch) p.tiles.push_back(z << 20 | k << 14 | ch);
+    }
+  for (int g = 0; 1 + g * Z <= N - 3; ++g)
+    for (int k = band_kmin(1 + g * Z); k < KB; ++k) p.cta.push_back(g << 16 | k);
+  return p;
+}
+
+ilu_status upload_band(ilu_tet t, int requested_slabs) {
+  const int N = t->host.N;
+  const int layers = std::max(1, N - 3);
+  int Z = 8;
+  if (requested_slabs > 0) Z = std::min(8, std::max(1, (layers + requested_slabs - 1) / requested_slabs));
+  BandPlan p = make_band_plan(N, Z);
+  t->band_Z = Z;
+  t->band_ncta = (int)p.cta.size();
+  t->band_ntiles = (int)p.tiles.size();
+  const size_t ni = p.cta.size() + p.tiles.size() + 3 + 2 + 1;
+  std::vector<int> ints;
+  ints.reserve(ni);
+  ints.insert(ints.end(), p.cta.begin(), p.cta.end());
+  ints.insert(ints.end(), p.tiles.begin(), p.tiles.end());
+  const size_t at_map = ints.size();
+  ints.push_back(0); ints.push_back(t->band_ncta); ints.push_back(0);  // CTA prefix {0, ncta}, order {0}
+  const size_t at_tp = ints.size();
+  ints.push_back(0); ints.push_back(t->band_ntiles);  // tile prefix
+  const size_t at_epoch = ints.size();
+  ints.push_back(0);
+  CK(cudaMalloc(&t->d_binfo, sizeof(BandInfo) * std::max<size_t>(p.info.size(), 1)), "cudaMalloc band tables");
+  if (!p.info.empty())
+    CK(cudaMemcpy(t->d_binfo, p.info.data(), sizeof(BandInfo) * p.info.size(), cudaMemcpyHostToDevice), "upload band tables");
+  CK(cudaMalloc(&t->d_bint, sizeof(int) * ints.size()), "cudaMalloc band tables");
+  CK(cudaMemcpy(t->d_bint, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice), "upload band tables");
+  CK(cudaMalloc(&t->d_bw, sizeof(float) * std::max<int64_t>(p.wfloats, 1)), "cudaMalloc band array");
+  CK(cudaMemset(t->d_bw, 0, sizeof(float) * std::max<int64_t>(p.wfloats, 1)), "cudaMemset band array");
+  CK(cudaMalloc(&t->d_bstreams, sizeof(unsigned long long) * std::max<int64_t>(p.swords, 2)), "cudaMalloc streams");
+  CK(cudaMemset(t->d_bstreams, 0, sizeof(unsigned long long) * std::max<int64_t>(p.swords, 2)), "cudaMemset streams");
+  BandDev &b = t->dev.band;
+  b.info = t->d_binfo;
+  b.cta = t->d_bint;
+  b.tiles = t->d_bint + p.cta.size();
+  b.w = t->d_bw;
+  b.streams = t->d_bstreams;
+  b.epoch = t->d_bint + at_epoch;
+  b.ncta = t->band_ncta;
+  b.ntiles = t->band_ntiles;
+  b.Z = Z;
+  t->nblocks = std::max(t->nblocks, t->band_ntiles);
+  BandLaunch &L = t->bl;
+  L.tets = t->d_dev;
+  L.ctas = t->band_ncta;
+  L.Z = Z;
+  L.reg = t->host.dx;
+  L.map_f = {t->d_bint + at_map, t->d_bint + at_map + 2, 1, t->d_flags + t->dev.fwd.ticket, nullptr, nullptr};
+  L.map_b = {t->d_bint + at_map, t->d_bint + at_map + 2, 1, t->d_flags + t->dev.bwd.ticket, nullptr, nullptr};
+  t->band_tprefix = t->d_bint + at_tp;
+  return ILU_OK;
+}
+
 ilu_status upload(ilu_tet t) {
   HostTet &h = t->host;
   CK(cudaSetDevice(t->device), "cudaSetDevice");
@@ -201,10 +296,18 @@ ilu_status upload(ilu_tet t) {
   CK(cudaMalloc(&t->d_status, sizeof(LaunchStatus)), "cudaMalloc status");
   CK(cudaMemset(t->d_status, 0, sizeof(LaunchStatus)), "cudaMemset status");
   CK(cudaMallocHost(&t->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
-  CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
   CK(cudaMalloc(&t->d_map, sizeof(int) * 5), "cudaMalloc cluster map");
   std::memset(t->h_status, 0, sizeof(LaunchStatus));
   t->nblocks = std::max(1, residual_blocks(h.N));
+  CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
+  // band kernels: measured faster than the slab kernels from level 9 on
+  // (L7/L8/L9 MIXED sweeps: 0.78/1.77/10.2 ms slab, 1.10/2.19/6.0 ms band)
+  t->use_band = t->precision != ILU_F64 && wave_uses_registers(t->kind(), h.dx) &&
+                (t->kernel_choice == ILU_KERNEL_BAND || (t->kernel_choice == ILU_KERNEL_AUTO && h.L >= 9));
+  if (t->use_band) {
+    ilu_status bs = upload_band(t, t->requested_slabs);
+    if (bs != ILU_OK) return bs;
+  }
   CK(cudaMalloc(&t->d_partials, sizeof(double) * t->nblocks), "cudaMalloc partials");
   t->norms_cap = 0;
   DevTet &d = t->dev;
@@ -310,6 +413,29 @@ struct Traced {
 // one sweep on device vectors: residual into w, forward, backward with x += w
 ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStream_t st) {
   CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * t->nflags, st), "reset flags");
+  if (t->use_band) {
+    {
+      Traced tr(t, 0, st);
+      CK(launch_band_in(t->kind(), 0, t->d_dev, t->band_tprefix, 1, t->band_ntiles, nullptr, nullptr, x, b,
+                        t->d_partials, st),
+         "residual launch");
+    }
+    if (d_norm_out) {
+      t->launches++;
+      CK(launch_norm_finish(t->d_partials, t->band_ntiles, d_norm_out, st), "norm launch");
+    }
+    {
+      Traced tr(t, 1, st);
+      CK(launch_band_sub(true, t->bl, t->d_status, t->max_spins, st), "forward launch");
+    }
+    {
+      Traced tr(t, 2, st);
+      CK(launch_band_sub(false, t->bl, t->d_status, t->max_spins, st), "backward launch");
+      t->launches++;
+      CK(launch_band_update(t->kind(), t->d_dev, t->band_tprefix, 1, t->band_ntiles, nullptr, x, st), "update launch");
+    }
+    return ILU_OK;
+  }
   int used = 0;
   {
     Traced tr(t, 0, st);
@@ -338,6 +464,24 @@ ilu_status precond(ilu_tet t, const void *r, void *z, cudaStream_t st) {
   const bool vf64 = t->precision != ILU_F32;   // Krylov vectors
   const bool wf64 = t->precision == ILU_F64;   // sweep scratch
   CK(cudaMemsetAsync(t->d_flags, 0, sizeof(int) * t->nflags, st), "reset flags");
+  if (t->use_band) {
+    t->launches++;
+    CK(launch_band_in(t->kind(), 1, t->d_dev, t->band_tprefix, 1, t->band_ntiles, nullptr, nullptr, r, nullptr,
+                      nullptr, st),
+       "copy launch");
+    CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
+    {
+      Traced tr(t, 1, st);
+      CK(launch_band_sub(true, t->bl, t->d_status, t->max_spins, st), "forward launch");
+    }
+    {
+      Traced tr(t, 2, st);
+      CK(launch_band_sub(false, t->bl, t->d_status, t->max_spins, st), "backward launch");
+      t->launches++;
+      CK(launch_band_update(t->kind(), t->d_dev, t->band_tprefix, 1, t->band_ntiles, nullptr, z, st), "update launch");
+    }
+    return ILU_OK;
+  }
   CK(launch_copy(vf64, wf64, r, t->d_w, n, st), "copy launch");
   CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
   {
@@ -415,6 +559,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->slabs = 0;
   o->device = 0;
   o->max_wait_spins = 0;
+  o->kernel = ILU_KERNEL_AUTO;
   return ILU_OK;
 }
 
@@ -447,6 +592,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   ilu_opts_default(&o);
   if (opts) o = *opts;
   if (o.precision < 0 || o.precision > 2) return fail(ILU_EINVAL, "unknown precision");
+  if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_BAND) return fail(ILU_EINVAL, "unknown kernel choice");
   int deg[3];
   for (int c = 0; c < 3; ++c) deg[c] = o.deg[c] >= 0 ? o.deg[c] : poly_degree;
   ilu_tet t = new (std::nothrow) ilu_tet_s;
@@ -479,6 +625,8 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
       return fail(ILU_ENODEV, "no CUDA device with that ordinal");
     }
     choose_geometry(t, o.slabs);
+    t->requested_slabs = o.slabs;
+    t->kernel_choice = o.kernel;
     st = upload(t);
     if (st != ILU_OK) {
       free_device(t);

@@ -78,6 +78,30 @@ ILU_HD int64_t row_id(int N, int y, int z) {
 // interior x-range of row (y,z) is [1, N-1-y-z]; its centre
 ILU_HD int row_len(int N, int y, int z) { return N - 1 - y - z; }
 
+// ---- bands: the FP32 sweeps give each lane of a warp one row.  Band k of
+// layer z holds the 32 rows y = band_Y(z,k) + j, j = 0..31 (rows outside
+// [1, N-2-z] are idle lanes).  The bands slant by one row per layer, so that
+// band k of layer z depends only on bands k-1 and k of layers z and z-1 in
+// the forward substitution (and on k, k+1 of z, z+1 in the backward one).
+// At step s lane j works on x = s - 2j: all lanes of a band are on the same
+// hyperplane x + 2y + 3z = s + band_level0(z,k).
+ILU_HD int band_kmax(int N) { return (N - 3) >> 5; }
+ILU_HD int band_kmin(int z) { return z >> 5; }
+ILU_HD int band_Y(int z, int k) { return 32 * k - z + 1; }
+ILU_HD int band_level0(int z, int k) { return 2 * band_Y(z, k) + 3 * z; }
+// first and last step with an interior point
+ILU_HD int band_slo(int z, int k) {
+  const int Y = band_Y(z, k);
+  return 1 + 2 * (Y >= 1 ? 0 : 1 - Y);
+}
+ILU_HD int band_shi(int N, int z, int k) {
+  const int Y = band_Y(z, k);
+  int jh = N - 2 - z - Y;
+  if (jh > 31) jh = 31;
+  return N - 1 - Y - z + jh;
+}
+ILU_HD bool band_exists(int N, int z, int k) { return z >= 1 && z <= N - 3 && k >= band_kmin(z) && k <= band_kmax(N); }
+
 // Edge-star pattern of the variable-coefficient stencil.  With element values
 // kappa_T = mean of the vertex values, A^p_d = sum_q W[d][q] kappa(p+q), where
 // q runs over the neighbours that share a micro-tetrahedron with the edge

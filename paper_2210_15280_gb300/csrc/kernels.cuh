@@ -19,6 +19,23 @@ struct WaveGeom {
   int zb, wpl, P, csize, prog, ticket;
 };
 
+// Band layout of the FP32 sweeps (band.cu): per band (z,k), index
+// (z-1) * (band_kmax(N)+1) + k, the offset of its [step-1][32] block in the
+// band array, of its edge stream and of the stream to the next CTA (or -1).
+struct BandInfo {
+  int64_t off, hoff, voff;
+};
+
+struct BandDev {
+  const BandInfo *info;
+  const int *cta;     // CTAs in dependency order: group << 16 | band
+  const int *tiles;   // residual/update tiles: z << 20 | k << 14 | chunk
+  void *w;            // band array (float)
+  unsigned long long *streams;  // tagged words exchanged between CTAs
+  int *epoch;         // launch tag counter (bumped by the first tile kernel of a sweep)
+  int ncta, ntiles, Z;
+};
+
 // Everything a kernel needs to know about one tet.  Plain old data so that it
 // can live in a device array for batched launches.
 struct DevTet {
@@ -35,6 +52,7 @@ struct DevTet {
   int *flags;        // progress words of the slabs and the two ticket counters
   double A15[15];    // constant stencil
   double Wstar[100]; // edge-star weights (variable coefficient)
+  BandDev band;      // FP32 band sweeps (null info when not used)
 };
 
 struct LaunchStatus {
@@ -102,6 +120,31 @@ size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool
 // (CTAs of at most 16 warps); otherwise they are read from shared memory.
 bool wave_uses_registers(int kind, int dx);
 int residual_blocks(int N);
+
+// ---- FP32 band sweeps (band.cu)
+
+// One forward or backward band launch over one or more tets: tickets map to
+// (tet, CTA) through map.prefix (CTAs per tet) and map.order.
+struct BandLaunch {
+  const DevTet *tets;
+  BatchMap map_f, map_b;
+  int ctas;  // total CTAs
+  int Z;     // warps (layers) per CTA, 1..8
+  int reg;   // row degree held in registers, 0..7 (rstride 4 for <= 3, else 8)
+};
+size_t band_smem_bytes(int Z);
+cudaError_t launch_band_sub(bool forward, const BandLaunch &L, LaunchStatus *status, long long max_spins,
+                            cudaStream_t st);
+// tiles of all tets (tet i owns tiles [tprefix[i], tprefix[i+1])): mode 0
+// r = b - A x into the band array (with per-tile ||r||^2 in partials, may be
+// null), mode 1 copy of x into the band array.  xs/bs: device arrays of
+// per-tet pointers, or null and x1/b1 for a single tet.
+cudaError_t launch_band_in(int kind, int mode, const DevTet *tets, const int *tprefix, int ntets, int total_tiles,
+                           const void *const *xs, const void *const *bs, const void *x1, const void *b1,
+                           double *partials, cudaStream_t st);
+// x += band array (per tet)
+cudaError_t launch_band_update(int kind, const DevTet *tets, const int *tprefix, int ntets, int total_tiles,
+                               void *const *xs, void *x1, cudaStream_t st);
 
 // ---- host-side views shared by the entry-point files (capi.cu defines them)
 

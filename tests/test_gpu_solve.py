@@ -31,14 +31,15 @@ def exact_solution(orc, pr, N, b, xbd):
     return x
 
 
-@pytest.mark.parametrize("prec", ["F64", "MIXED"])
+@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND")])
 @pytest.mark.parametrize("method", ["RICHARDSON", "PCG"])
-def test_solve_reaches_tolerance(g, orc, prec, method):
+def test_solve_reaches_tolerance(g, orc, prec, method, kernel):
     level, deg, N = 4, 4, 16
     P = si.macro_tet(101)
     co = ("sinprod", 1.0, 0.5, 0)
     pr = orc.Problem(P, level, orc.Coeff(*co), deg=deg)
-    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=getattr(g, prec))
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=getattr(g, prec),
+              kernel=getattr(g, "KERNEL_" + kernel))
     t.import_surrogate(pr.coefs)
     b = si.rhs(level, 102)
     xbd = np.zeros(len(b))

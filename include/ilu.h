@@ -198,7 +198,11 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 
 /* Group tets for smoothing together.  All tets must live on one device and
  * share one precision; levels and degrees may differ.  opts (nullable) may set
- * slabs (wavefront partition, as in ilu_setup) and max_wait_spins.  The batch
+ * max_wait_spins and slabs: > 0 fixes the wavefront partition of every tet
+ * (as in ilu_setup); otherwise the batch autotunes it, timing one pass of
+ * the batch for each candidate (layers per slab CTA 1, 2, 4 x cluster size
+ * for most resident CTAs or largest) on scratch vectors and keeping the
+ * fastest.  Batches use the slab substitution kernels.  The batch
  * keeps references to the tets, which must outlive it; it reuses each tet's
  * scratch, so a tet must not be smoothed by another call while a batch call
  * on it runs.  ILU_EINVAL for an empty batch, a null or failed tet, or mixed

@@ -80,35 +80,57 @@ struct ilu_batch_s {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_sweeps = 0;
+  int tuned_zb = 0;  // autotuner's choice (0: not tuned)
+  int explicit_slabs = 0;
+  bool tuned_largest = false;
+  double tuned_ms = -1;
 };
 
 namespace {
 
-void release(ilu_batch b) {
-  if (!b) return;
+// device state of one launch plan (rebuilt while autotuning)
+void free_plan(ilu_batch b) {
   cudaSetDevice(b->device);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_sweeps = 0;
   for (auto &g : b->groups) {
     if (g.st) cudaStreamDestroy(g.st);
     if (g.done) cudaEventDestroy(g.done);
   }
+  b->groups.clear();
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->ptr_ev) cudaEventDestroy(b->ptr_ev);
   if (b->fork) cudaEventDestroy(b->fork);
+  b->cap = nullptr;
+  b->ptr_ev = b->fork = nullptr;
   cudaFree(b->d_tets);
   cudaFree(b->d_bprefix);
   cudaFree(b->d_maps);
   cudaFree(b->d_flags);
   cudaFree(b->d_ptrs);
   cudaFree(b->d_status);
+  b->d_tets = nullptr;
+  b->d_bprefix = b->d_maps = b->d_flags = nullptr;
+  b->d_ptrs = nullptr;
+  b->d_status = nullptr;
   if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
   if (b->h_status) cudaFreeHost(b->h_status);
+  b->h_ptrs = nullptr;
+  b->h_status = nullptr;
+}
+
+void release(ilu_batch b) {
+  if (!b) return;
+  free_plan(b);
   delete b;
 }
 
 // Build groups, per-tet geometry and flag layout, device arrays and the
-// launch shapes (cluster size: the most resident CTAs, larger clusters on ties).
-ilu_status build(ilu_batch b, int requested_slabs) {
+// launch shapes.  zb: layers per slab CTA (0: the single-tet default);
+// largest: clusters as large as the device schedules (fewer slow hops
+// between clusters), else the size with the most resident CTAs.
+ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   const int n = b->n;
   // groups keyed by (level, register degree class, padded row length)
   std::map<std::tuple<int, int, int>, int> key;
@@ -141,8 +163,10 @@ ilu_status build(ilu_batch b, int requested_slabs) {
     for (int i : g.members) {
       const TetView &v = b->views[i];
       DevTet d = *v.dev;
-      d.fwd = wave_geom(v.N, v.kind, v.rstride, v.dx, true, requested_slabs);
-      d.bwd = wave_geom(v.N, v.kind, v.rstride, v.dx, false, requested_slabs);
+      const int layers = std::max(1, v.N - 3);
+      const int requested = b->explicit_slabs > 0 ? b->explicit_slabs : (zb_pref > 0 ? (layers + zb_pref - 1) / zb_pref : 0);
+      d.fwd = wave_geom(v.N, v.kind, v.rstride, v.dx, true, requested);
+      d.bwd = wave_geom(v.N, v.kind, v.rstride, v.dx, false, requested);
       d.fwd.prog = off;
       d.bwd.prog = off + d.fwd.P;
       off += d.fwd.P + d.bwd.P;
@@ -194,7 +218,8 @@ ilu_status build(ilu_batch b, int requested_slabs) {
     int qf[1 + kClusterCands] = {}, qb[1 + kClusterCands] = {};
     BK(launch_forward(L, nullptr, 0, nullptr, qf), "cluster query");
     BK(launch_backward(L, nullptr, 0, nullptr, qb), "cluster query");
-    auto best = [](const int *q, int maxP) {
+    auto best = [largest](const int *q, int maxP) {
+      if (largest) return q[0];
       int cs = 1, res = 0;
       for (int i = 0; i < kClusterCands; ++i) {
         const int c = std::min(kClusterSizes[i], maxP);
@@ -253,6 +278,65 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
     }
   }
   return ILU_OK;
+}
+
+// One pass of every group on scratch vectors (the tets' scratch and tables
+// are real, x and b are a shared scratch buffer: the values are of no use,
+// the timing is that of a sweep).  Returns milliseconds, or < 0 on failure.
+double time_pass(ilu_batch b, void *scratch) {
+  for (int i = 0; i < b->n; ++i) {
+    b->h_ptrs[i] = scratch;
+    b->h_ptrs[b->n + i] = scratch;
+  }
+  if (cudaMemcpy(b->d_ptrs, b->h_ptrs, sizeof(void *) * 2 * b->n, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = -1;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, b->cap);
+    if (record_passes(b, 1) != ILU_OK) break;
+    cudaEventRecord(e1, b->cap);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best < 0 || ms < best)) best = ms;  // the first pass warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaMemcpy(b->h_status, b->d_status, sizeof(LaunchStatus), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      b->h_status->code != 0)
+    return -1;
+  return best;
+}
+
+// Autotuner: layers per slab CTA x cluster policy, timed on the batch itself.
+ilu_status tune(ilu_batch b) {
+  size_t nmax = 0;
+  for (const auto &v : b->views) nmax = std::max(nmax, v.nnodes);
+  void *scratch = nullptr;
+  BK(cudaMalloc(&scratch, nmax * sizeof(double)), "cudaMalloc tuning scratch");
+  BK(cudaMemset(scratch, 0, nmax * sizeof(double)), "cudaMemset tuning scratch");
+  int best_zb = 0;
+  bool best_largest = false;
+  double best_ms = -1;
+  for (int zb : {1, 2, 4})
+    for (bool largest : {false, true}) {
+      free_plan(b);
+      if (build(b, zb, largest) != ILU_OK) continue;
+      const double ms = time_pass(b, scratch);
+      if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+        best_ms = ms;
+        best_zb = zb;
+        best_largest = largest;
+      }
+    }
+  cudaFree(scratch);
+  free_plan(b);
+  b->tuned_zb = best_zb;
+  b->tuned_largest = best_largest;
+  b->tuned_ms = best_ms;
+  return build(b, best_zb, best_largest);
 }
 
 ilu_status capture(ilu_batch b, int sweeps) {
@@ -315,7 +399,13 @@ ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, il
     delete b;
     return fail(ILU_ECUDA, "cudaSetDevice");
   }
-  ilu_status st = build(b, opts ? opts->slabs : 0);
+  ilu_status st;
+  if (opts && opts->slabs > 0) {
+    b->explicit_slabs = opts->slabs;  // an explicit partition, as ilu_opts.slabs for one tet
+    st = build(b, 0, false);
+  } else {
+    st = tune(b);
+  }
   if (st != ILU_OK) {
     const std::string msg = ilu_last_error();
     release(b);

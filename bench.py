@@ -10,6 +10,17 @@ and update), b ~ U(-1, 1) (seed 4), x0 = 0.  Inputs are smaller than L2, so a
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
+
+Two further workloads print a line of the same form (not the default run):
+  --workload batch   256 macro-tets of a jittered 4x4x3 cube mesh (aspect
+                     ratio <= 3), levels U{5..8}, degrees U{4..6}, FP32,
+                     kappa = 1; one step = one sweep of the whole batch (one
+                     CUDA-graph replay, autotuned partition).
+  --workload serve   the request loop: Poisson arrivals (mean gap 0.5 ms) of
+                     interior solves on macro-tets of that mesh, levels 5-6
+                     (Richardson) or 5-8 (--method pcg), mixed coefficients,
+                     to 1e-8; solves/s and p50/p99 latency, beside the same
+                     requests solved one after another with FP64 sweeps.
 """
 import argparse
 import json
@@ -174,6 +185,139 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def batch_workload(args, g, torch):
+    """256 tets, one autotuned batch, one graph replay per step."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = 256
+    mesh = si.macro_mesh(6, n_tets=n)
+    levels = si.batch_levels(7, n, 5, 8)
+    degs = 4 + (si.splitmix64(9, n) % 3).astype(int)
+    with ThreadPoolExecutor(8) as ex:
+        tets = list(ex.map(lambda i: g.Tet(mesh[i], int(levels[i]), coeff=g.make_coeff("const"),
+                                           poly_degree=int(degs[i]), precision=g.F32), range(n)))
+    idof = sum(interior(int(L)) for L in levels)
+    xs = [torch.zeros(si.num_nodes(int(L)), dtype=torch.float32, device="cuda") for L in levels]
+    bh = [si.rhs(int(L), 100 + i).astype(np.float32) for i, L in enumerate(levels)]
+    bs = [torch.tensor(v, device="cuda") for v in bh]
+    B = g.Batch(tets)
+    W, K = max(3, args.warmup), max(1, args.steps)
+    for _ in range(W):
+        B.smooth(xs, bs, 1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stream = torch.cuda.current_stream()
+    for k in range(K):  # inputs (~4 GB) exceed L2: no flush needed
+        ev[k][0].record(stream)
+        B.smooth(xs, bs, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b2) for a, b2 in ev)
+    value = idof * K / (total_ms / 1e3)
+    # end to end: host vectors copied in and the result copied out every step
+    xh = [np.zeros(v.numel(), dtype=np.float32) for v in xs]
+    bhp = [torch.from_numpy(v).pin_memory() for v in bh]
+    xhp = [torch.from_numpy(v).pin_memory() for v in xh]
+    E = max(2, min(K, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        for d, h in zip(xs, xhp):
+            d.copy_(h, non_blocking=True)
+        for d, h in zip(bs, bhp):
+            d.copy_(h, non_blocking=True)
+        B.smooth(xs, bs, 1)
+        for d, h in zip(xs, xhp):
+            h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e = idof * E / (time.perf_counter() - t0)
+    nbytes = sum(v.numel() for v in xs) * 4
+    achieved = idof * 24 / (total_ms / K / 1e3) / 1e9  # F32 sweep: 24 algorithmic bytes per DoF
+    hbm, src = peaks()
+    return {"metric": "smoother DoF-sweeps/s (batch of 256 macro-tets, FP32 sweeps)", "value": value, "unit": UNIT,
+            "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch of {n} macro-tets, levels 5-8, degrees 4-6, {idof} interior DoF",
+                       "tuned": "autotuned partition", "l2": "inputs larger than L2", "parallelism": "replicas x1"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": None,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "whole sweep (residual + forward + backward)", "peak_source": src},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]}}
+
+
+def serve_workload(args, g, torch):
+    """Poisson stream of interior solves through the request loop, against the
+    same requests solved one after another with FP64 sweeps."""
+    pcg = args.method == "pcg"
+    nreq = args.requests
+    pool = si.macro_mesh(6, n_tets=32)
+    lo, hi = (5, 8) if pcg else (5, 6)
+    levels = si.batch_levels(11, nreq, lo, hi)
+    kinds = [("const", 1.0, 0.0, 0), ("sinprod", 1.0, 0.5, 0), ("kappa_i", 0.0, 0.0, 2)]
+    which = si.splitmix64(12, nreq) % len(pool)
+    arrivals = si.poisson_arrivals(13, nreq, 0.5e-3)  # seconds from the first submit
+    method = g.PCG if pcg else g.RICHARDSON
+    reqs = []
+    for i in range(nreq):
+        L = int(levels[i])
+        reqs.append(dict(P=pool[int(which[i])], level=L, co=kinds[int(which[i]) % 3], b=si.rhs(L, 1000 + i)))
+    # every distinct tet set up once before the timed stream (resident afterwards)
+    warm = {}
+    for r in reqs:
+        warm.setdefault((id(r["P"]), r["level"], r["co"]), r)
+    s = g.Server(precision=g.MIXED, max_slots=64)
+    for tk in [s.submit(r["P"], r["level"], r["b"], coeff=g.make_coeff(*r["co"]), poly_degree=5, method=method)
+               for r in warm.values()]:
+        s.wait(tk)
+    t0 = time.perf_counter()
+    tks = []
+    for i, r in enumerate(reqs):
+        target = t0 + float(arrivals[i])
+        while time.perf_counter() < target:
+            pass
+        tks.append(s.submit(r["P"], r["level"], r["b"], coeff=g.make_coeff(*r["co"]), poly_degree=5, method=method))
+    lat, ok = [], 0
+    for tk in tks:
+        res = s.wait(tk)
+        ok += res["status"] == g.ILU_OK
+        lat.append(res["latency_ms"])
+    wall = time.perf_counter() - t0
+    st = s.stats()
+    s.close()
+    lat = np.sort(np.array(lat))
+    # the same requests, one after another, FP64 sweeps, tets set up beforehand
+    seq = {}
+    for r in reqs:
+        key = (id(r["P"]), r["level"], r["co"])
+        if key not in seq:
+            seq[key] = g.Tet(r["P"], r["level"], coeff=g.make_coeff(*r["co"]), poly_degree=5, precision=g.F64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in reqs:
+        t = seq[(id(r["P"]), r["level"], r["co"])]
+        x = torch.zeros(si.num_nodes(r["level"]), dtype=torch.float64, device="cuda")
+        b = torch.tensor(r["b"], dtype=torch.float64, device="cuda")
+        t.solve(x, b, method, 1e-8, 100000)
+        x.cpu()
+    seq_rate = nreq / (time.perf_counter() - t1)
+    q = lambda p: float(lat[min(len(lat) - 1, max(0, int(np.ceil(p * len(lat))) - 1))])
+    return {"metric": "served interior solves/s (request loop, p50/p99 latency)", "value": nreq / wall,
+            "unit": "solves/s", "n_gpus": 1, "steps": nreq, "warmup": len(warm), "ms_per_step": 1e3 * wall / nreq,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{nreq} Poisson-arrival requests (mean gap 0.5 ms), levels {lo}-{hi}, "
+                                   f"{'PCG' if pcg else 'Richardson'} to 1e-8, MIXED, 32 macro-tets x 3 kappa",
+                       "parallelism": "replicas x1"},
+            "p50_ms": q(0.5), "p99_ms": q(0.99), "completed": ok, "max_concurrent": st["max_concurrent"],
+            "sequential_f64_solves_per_s": seq_rate,
+            "e2e": {"value": nreq / wall, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +325,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--method", default="richardson", choices=["richardson", "pcg"])
+    ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -191,6 +338,11 @@ def main():
     import torch
     import paper_2210_15280_gb300 as g
     torch.cuda.set_device(local)
+    if args.workload != "single":
+        if rank == 0:
+            line = (batch_workload if args.workload == "batch" else serve_workload)(args, g, torch)
+            print(json.dumps(line), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

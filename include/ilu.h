@@ -174,7 +174,7 @@ ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double
  * acceptable).  The paper has no counterpart.  The caller passes x, b (device,
  * the handle's vector type), r (device, same type; required: boundary entries
  * set to 0) and norm_dev (device, one double receiving ||r||_2).  The only
- * scratch, the per-block partial sums of the norm, lives in a fixed 512 KiB
+ * scratch, the per-block partial sums of the norm, lives in a fixed 1 MiB
  * device array inside the library: levels above 9 are rejected with
  * ILU_EINVAL.  The array is shared by all calls on a device and keeps the last
  * call's contents (every entry used is written before it is read); calls whose

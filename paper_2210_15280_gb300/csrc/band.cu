@@ -35,6 +35,7 @@
 
 #include "../../include/ilu.h"
 #include "kernels.cuh"
+#include "stencil.cuh"
 
 namespace ilu {
 
@@ -663,18 +664,6 @@ __global__ void __launch_bounds__(256, 2) bwd_band(const DevTet *__restrict__ te
 
 // residual at one interior point, operator from t (constant stencil or
 // on-the-fly edge-star assembly); FP64 for double x
-template <int E>
-__device__ __forceinline__ void star_term2(double *A, const double *kq, const double *W) {
-  constexpr int D = star_d(E);
-  constexpr int Q = star_q(E);
-  A[D] = fma(W[E], kq[Q], A[D]);
-}
-template <int... E>
-__device__ __forceinline__ void star_all2(std::integer_sequence<int, E...>, double *A, const double *kq,
-                                          const double *W) {
-  (star_term2<E>(A, kq, W), ...);
-}
-
 template <typename TX, typename TR, bool VAR>
 __device__ __forceinline__ TR residual_at(const DevTet &t, int N, int x, int y, int z, const TX *__restrict__ xv_,
                                           const TX *__restrict__ b) {
@@ -719,14 +708,7 @@ __device__ __forceinline__ TR residual_at(const DevTet &t, int N, int x, int y, 
     kq[12] = kap[rts + x];
     kq[13] = kap[rt + x];
     kq[14] = kap[rt + x - 1];
-    double A[15];
-#pragma unroll
-    for (int d = 0; d < 15; ++d) A[d] = 0.0;
-    star_all2(std::make_integer_sequence<int, 100>{}, A, kq, t.Wstar);
-    const double xc = (double)xv[7];
-#pragma unroll
-    for (int d = 0; d < 15; ++d)
-      if (d != 7) res = (TR)fma(-A[d], (double)xv[d] - xc, (double)res);
+    star_apply_all(std::make_integer_sequence<int, 15>{}, res, kq, xv, t.Wstar);
   }
   return res;
 }

@@ -67,6 +67,7 @@ struct ilu_tet_s {
   BandLaunch bl = {};
   const int *band_tprefix = nullptr;
   int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
+  int *d_chunks = nullptr;  // residual work list (32-point row chunks)
   WaveLaunch wl = {};       // the forward/backward launch shape of this tet
   LaunchStatus *d_status = nullptr, *h_status = nullptr;
   int nblocks = 0, norms_cap = 0;
@@ -100,8 +101,8 @@ void free_device(ilu_tet t) {
   t->ev_pool.clear();
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa);
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
-  cudaFree(t->d_dev); cudaFree(t->d_map);
-  t->d_dev = nullptr; t->d_map = nullptr;
+  cudaFree(t->d_dev); cudaFree(t->d_map); cudaFree(t->d_chunks);
+  t->d_dev = nullptr; t->d_map = nullptr; t->d_chunks = nullptr;
   cudaFree(t->d_binfo); cudaFree(t->d_bint); cudaFree(t->d_bw); cudaFree(t->d_bstreams);
   t->d_binfo = nullptr; t->d_bint = nullptr; t->d_bw = nullptr; t->d_bstreams = nullptr;
   cudaFree(t->d_xs); cudaFree(t->d_bs);
@@ -298,7 +299,17 @@ ilu_status upload(ilu_tet t) {
   CK(cudaMallocHost(&t->h_status, sizeof(LaunchStatus)), "cudaMallocHost status");
   CK(cudaMalloc(&t->d_map, sizeof(int) * 5), "cudaMalloc cluster map");
   std::memset(t->h_status, 0, sizeof(LaunchStatus));
-  t->nblocks = std::max(1, residual_blocks(h.N));
+  t->nblocks = std::max({1, residual_blocks(h.N), rowgrid_blocks(h.N)});
+  {
+    std::vector<int> chunks(residual_chunks(h.N));
+    residual_chunk_list(h.N, chunks.data());
+    CK(cudaMalloc(&t->d_chunks, sizeof(int) * std::max<size_t>(chunks.size(), 1)), "cudaMalloc residual chunks");
+    if (!chunks.empty())
+      CK(cudaMemcpy(t->d_chunks, chunks.data(), sizeof(int) * chunks.size(), cudaMemcpyHostToDevice),
+         "upload residual chunks");
+    t->dev.chunks = t->d_chunks;
+    t->dev.nchunks = (int)chunks.size();
+  }
   CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
   // band kernels: measured faster than the slab kernels from level 9 on
   // (L7/L8/L9 MIXED sweeps: 0.78/1.77/10.2 ms slab, 1.10/2.19/6.0 ms band)

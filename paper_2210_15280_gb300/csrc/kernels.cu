@@ -15,24 +15,11 @@
 #include <utility>
 
 #include "kernels.cuh"
+#include "stencil.cuh"
 
 namespace ilu {
 
 namespace {
-
-// ------------------------------------------- edge-star pattern (unrolled) --
-
-template <int E>
-__device__ __forceinline__ void star_term(double *A, const double *kq, const double *W) {
-  constexpr int D = star_d(E);
-  constexpr int Q = star_q(E);
-  A[D] = fma(W[E], kq[Q], A[D]);
-}
-template <int... E>
-__device__ __forceinline__ void star_all(std::integer_sequence<int, E...>, double *A, const double *kq,
-                                         const double *W) {
-  (star_term<E>(A, kq, W), ...);
-}
 
 // --------------------------------------------------------- small helpers --
 
@@ -41,10 +28,18 @@ __device__ __forceinline__ void star_all(std::integer_sequence<int, E...>, doubl
 // r = b - A x at the interior points of row (y, z), one warp; returns this
 // lane's share of ||r||^2.  A15/Wstar/kappa come from t (kernel parameter or
 // device memory).
+// where a row's operator comes from: the constant stencil, the edge-star
+// weights and kappa at the grid points
+struct StencilData {
+  const double *A15, *Wstar, *kappa;
+};
+
+// r = b - A x at the interior points x0 + lane of row (y, z) (one warp, one
+// 32-point chunk of the row); returns this lane's share of ||r||^2
 template <typename TX, typename TR, typename TW, bool VAR>
-__device__ __forceinline__ double residual_row(const DevTet &t, int N, int y, int z, int lane,
-                                               const TX *__restrict__ x, const TX *__restrict__ b,
-                                               TW *__restrict__ r) {
+__device__ __forceinline__ double residual_chunk(const StencilData &t, int N, int y, int z, int x0, int lane,
+                                                 const TX *__restrict__ x, const TX *__restrict__ b,
+                                                 TW *__restrict__ r) {
   double acc2 = 0.0;
   if (y + z > N - 2) return acc2;
   const int n = N - 1 - y - z;
@@ -56,7 +51,9 @@ __device__ __forceinline__ double residual_row(const DevTet &t, int N, int y, in
   const int64_t rbn = grid_index(N, 0, y + 1, z - 1); // (y+1, z-1)
   const int64_t rt = grid_index(N, 0, y, z + 1);      // (y, z+1)
   const int64_t rts = grid_index(N, 0, y - 1, z + 1); // (y-1, z+1)
-  for (int xx = 1 + lane; xx <= n; xx += 32) {
+  {
+    const int xx = x0 + lane;
+    if (xx > n) return acc2;
     // neighbour values in the order of D: w s se bnw bn bc be c e n nw tse ts tc tw
     TR xv[15];
     xv[0] = (TR)x[r0 + xx - 1];
@@ -96,15 +93,7 @@ __device__ __forceinline__ double residual_row(const DevTet &t, int N, int y, in
       kq[12] = kap[rts + xx];
       kq[13] = kap[rt + xx];
       kq[14] = kap[rt + xx - 1];
-      double A[15];
-#pragma unroll
-      for (int d = 0; d < 15; ++d) A[d] = 0.0;
-      star_all(std::make_integer_sequence<int, 100>{}, A, kq, t.Wstar);
-      // rows sum to zero: (A x)_p = sum_{d != c} A_d (x_{p+d} - x_p)
-      const double xc = (double)xv[7];
-#pragma unroll
-      for (int d = 0; d < 15; ++d)
-        if (d != 7) res = (TR)fma(-A[d], (double)xv[d] - xc, (double)res);
+      star_apply_all(std::make_integer_sequence<int, 15>{}, res, kq, xv, t.Wstar);
     }
     r[r0 + xx] = (TW)res;
     acc2 += (double)res * (double)res;
@@ -112,13 +101,20 @@ __device__ __forceinline__ double residual_row(const DevTet &t, int N, int y, in
   return acc2;
 }
 
-// One tet: grid ((N-3+7)/8, N-3), one warp per row, per-block partial norms.
+// One tet: one warp per 32-point chunk of an interior row (the chunk list
+// balances rows of every length), 8 chunks per block, per-block partial norms.
 template <typename TX, typename TR, typename TW, bool VAR>
 __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__restrict__ x,
                                                        const TX *__restrict__ b, TW *__restrict__ r,
                                                        double *__restrict__ partials) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc2 = residual_row<TX, TR, TW, VAR>(t, t.N, blockIdx.x * 8 + warp + 1, blockIdx.y + 1, lane, x, b, r);
+  const StencilData sd{t.A15, t.Wstar, t.kappa};
+  const int ci = blockIdx.x * 8 + warp;
+  double acc2 = 0.0;
+  if (ci < t.nchunks) {
+    const int ch = t.chunks[ci];
+    acc2 = residual_chunk<TX, TR, TW, VAR>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b, r);
+  }
   // deterministic block reduction of the squared norm
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
@@ -128,7 +124,7 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int k = 0; k < 8; ++k) s += red[k];
-    partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+    partials[blockIdx.x] = s;
   }
 }
 
@@ -146,16 +142,25 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
     if (bprefix[mid] <= blk) lo = mid;
     else hi = mid - 1;
   }
-  const DevTet &t = tets[lo];
-  const int N = t.N;
-  const int gx = (N - 3 + 7) / 8, local = blk - bprefix[lo];
-  const int by = local / gx, bx = local - by * gx;
+  const DevTet &tg = tets[lo];
+  // the block's stencil weights in shared memory (reading them from the
+  // device array would keep all 100 live in registers)
+  __shared__ double sW[kStarPairs], sA[15];
+  for (int i = threadIdx.x; i < kStarPairs; i += blockDim.x) sW[i] = tg.Wstar[i];
+  if (threadIdx.x < 15) sA[threadIdx.x] = tg.A15[threadIdx.x];
+  __syncthreads();
+  const int N = tg.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  TW *r = reinterpret_cast<TW *>(t.w);
-  if (t.const_kappa)
-    residual_row<TX, TR, TW, false>(t, N, bx * 8 + warp + 1, by + 1, lane, xs[lo], bs[lo], r);
+  const int ci = (blk - bprefix[lo]) * 8 + warp;
+  if (ci >= tg.nchunks) return;  // no block-wide synchronisation follows
+  const int ch = tg.chunks[ci];
+  TW *r = reinterpret_cast<TW *>(tg.w);
+  const StencilData sd{sA, sW, tg.kappa};
+  const int y = (ch >> 10) & 1023, z = ch >> 20, x0 = 1 + 32 * (ch & 1023);
+  if (tg.const_kappa)
+    residual_chunk<TX, TR, TW, false>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
   else
-    residual_row<TX, TR, TW, true>(t, N, bx * 8 + warp + 1, by + 1, lane, xs[lo], bs[lo], r);
+    residual_chunk<TX, TR, TW, true>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
 }
 
 // ------------------------------------------------- solver vector helpers --
@@ -254,14 +259,29 @@ __global__ void norm_finish_kernel(const double *__restrict__ partials, int n, d
 
 // ------------------------------------------------------------ launchers --
 
-int residual_blocks(int N) { return ((N - 3 + 7) / 8) * (N - 3); }
+// 32-point chunks of the interior rows, z-major then y then chunk
+int residual_chunks(int N) {
+  int n = 0;
+  for (int z = 1; z <= N - 3; ++z)
+    for (int y = 1; y <= N - 2 - z; ++y) n += (N - 1 - y - z + 31) / 32;
+  return n;
+}
+int residual_blocks(int N) { return (residual_chunks(N) + 7) / 8; }
+int rowgrid_blocks(int N) { return ((N - 3 + 7) / 8) * (N - 3); }
+void residual_chunk_list(int N, int *out) {
+  int i = 0;
+  for (int z = 1; z <= N - 3; ++z)
+    for (int y = 1; y <= N - 2 - z; ++y)
+      for (int c = 0; c < (N - 1 - y - z + 31) / 32; ++c) out[i++] = z << 20 | y << 10 | c;
+}
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st) {
-  const int N = t.N;
-  dim3 grid((N - 3 + 7) / 8, N - 3);
-  if ((int)(grid.x * grid.y) > nblocks_cap) return cudaErrorInvalidValue;
-  if (nblocks_used) *nblocks_used = grid.x * grid.y;
+  const int nb = (t.nchunks + 7) / 8;
+  if (nb > nblocks_cap || !t.chunks) return cudaErrorInvalidValue;
+  if (nblocks_used) *nblocks_used = nb;
+  if (nb == 0) return cudaSuccess;
+  dim3 grid(nb);
   const bool var = !t.const_kappa;
   if (kind == kSweepF64) {
     if (var)

@@ -53,6 +53,8 @@ struct DevTet {
   double A15[15];    // constant stencil
   double Wstar[100]; // edge-star weights (variable coefficient)
   BandDev band;      // FP32 band sweeps (null info when not used)
+  const int *chunks; // residual work list: z << 20 | y << 10 | chunk (32 points of a row)
+  int nchunks;
 };
 
 struct LaunchStatus {
@@ -119,7 +121,10 @@ size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool
 // FP32/MIXED sweeps of degree <= 7 keep each row's polynomials in registers
 // (CTAs of at most 16 warps); otherwise they are read from shared memory.
 bool wave_uses_registers(int kind, int dx);
-int residual_blocks(int N);
+int residual_blocks(int N);  // blocks of the residual launch (8 row chunks each)
+int rowgrid_blocks(int N);   // blocks of the row-per-warp reductions (interior norm)
+int residual_chunks(int N);
+void residual_chunk_list(int N, int *out);
 
 // ---- FP32 band sweeps (band.cu)
 

@@ -12,7 +12,7 @@
 // contents; every partial sum it uses is written before it is read, so no
 // clearing is needed.  Calls whose kernels overlap on the GPU (different
 // streams, or several host threads) race on it: serialise them.  Every GPU
-// that loads the library holds the array (512 KiB) until the process exits.
+// that loads the library holds the array (1 MiB) until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,7 +29,7 @@ void set_last_error(const std::string &msg);
 
 namespace {
 
-constexpr int kMaxPartials = 65536;  // residual blocks up to level 9 (32,576 at level 9)
+constexpr int kMaxPartials = 131072;  // residual blocks up to level 9 (about 87,000 at level 9)
 static __device__ __align__(256) double g_partials[kMaxPartials];
 
 constexpr int kMaxDevices = 64;

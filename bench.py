@@ -11,7 +11,11 @@ and update), b ~ U(-1, 1) (seed 4), x0 = 0.  Inputs are smaller than L2, so a
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.
 
-Two further workloads print a line of the same form (not the default run):
+Further workloads print a line of the same form (not the default run):
+  --workload level9  one macro-tet at level 9 (22.1M interior DoF), kappa = 1,
+                     degree 6, F32 sweeps (band kernels) and, in the line's
+                     "f64" entry, FP64 sweeps; against the HBM roofline at
+                     24 (F32) and 56 (F64) algorithmic bytes per DoF.
   --workload batch   256 macro-tets of a jittered 4x4x3 cube mesh (aspect
                      ratio <= 3), levels U{5..8}, degrees U{4..6}, FP32,
                      kappa = 1; one step = one sweep of the whole batch (one
@@ -250,6 +254,50 @@ def batch_workload(args, g, torch):
                        "samples": clk["samples"]}}
 
 
+def level9_workload(args, g, torch):
+    """Single L9 tet, F32 and F64 sweeps, whole-sweep roofline."""
+    level = 9
+    nint = interior(level)
+    P = si.macro_tet(5)
+    out = {}
+    hbm, src = peaks()
+    W, K = max(3, args.warmup), max(1, min(args.steps, 20))
+    for prec, dt, bpd in [(g.F32, torch.float32, 24), (g.F64, torch.float64, 56)]:
+        t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=6, precision=prec)
+        b = torch.tensor(si.rhs(level, 6), dtype=dt, device="cuda")
+        x = torch.zeros_like(b)
+        t.smooth(x, b, W)
+        torch.cuda.synchronize()
+        t.profile(True)
+        t.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        t.smooth(x, b, K)  # vectors of 90-180 MB each exceed L2
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        kms, launches = t.profile_read()
+        achieved = nint * bpd / (ms / 1e3) / 1e9
+        out[prec] = {"value": nint / (ms / 1e3), "ms_per_step": ms, "achieved_gbs": achieved,
+                     "frac": achieved / hbm, "kernel_ms": [round(v / K, 4) for v in kms],
+                     "launches_per_step": launches / K}
+        t.close()
+    f = out[g.F32]
+    return {"metric": "smoother DoF-sweeps/s (single macro-tet, level 9, FP32 sweeps)", "value": f["value"],
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": f["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"single macro-tet L9 ({nint} interior DoF), kappa=1, deg 6",
+                       "kernels": "band (automatic choice at level 9)", "l2": "inputs larger than L2",
+                       "parallelism": "replicas x1"},
+            "roofline": {"bound": "hbm", "achieved": f["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": f["frac"], "traffic": None, "kernel": "whole sweep at 24 B/DoF",
+                         "peak_source": src, "kernel_ms_per_launch": f["kernel_ms"]},
+            "f64": {"value": out[g.F64]["value"], "ms_per_step": out[g.F64]["ms_per_step"],
+                    "achieved_gbs": out[g.F64]["achieved_gbs"], "frac": out[g.F64]["frac"],
+                    "kernel_ms_per_launch": out[g.F64]["kernel_ms"]},
+            "gpu_launches": int(round(f["launches_per_step"] * K))}
+
+
 def serve_workload(args, g, torch):
     """Poisson stream of interior solves through the request loop, against the
     same requests solved one after another with FP64 sweeps."""
@@ -325,7 +373,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg"])
     ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
@@ -340,7 +388,8 @@ def main():
     torch.cuda.set_device(local)
     if args.workload != "single":
         if rank == 0:
-            line = (batch_workload if args.workload == "batch" else serve_workload)(args, g, torch)
+            line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload}[args.workload](
+                args, g, torch)
             print(json.dumps(line), flush=True)
         return
     dist = None

@@ -664,12 +664,20 @@ __global__ void __launch_bounds__(256, 2) bwd_band(const DevTet *__restrict__ te
 
 // residual at one interior point, operator from t (constant stencil or
 // on-the-fly edge-star assembly); FP64 for double x
+// starts of the seven grid rows a point's stencil touches (one row (y, z))
+struct RowStarts {
+  int64_t r0, rs, rn, rb, rbn, rt, rts;
+};
+__device__ __forceinline__ RowStarts row_starts(int N, int y, int z) {
+  return {grid_index(N, 0, y, z),     grid_index(N, 0, y - 1, z), grid_index(N, 0, y + 1, z),
+          grid_index(N, 0, y, z - 1), grid_index(N, 0, y + 1, z - 1), grid_index(N, 0, y, z + 1),
+          grid_index(N, 0, y - 1, z + 1)};
+}
+
 template <typename TX, typename TR, bool VAR>
-__device__ __forceinline__ TR residual_at(const DevTet &t, int N, int x, int y, int z, const TX *__restrict__ xv_,
+__device__ __forceinline__ TR residual_at(const DevTet &t, const RowStarts &R, int x, const TX *__restrict__ xv_,
                                           const TX *__restrict__ b) {
-  const int64_t r0 = grid_index(N, 0, y, z), rs = grid_index(N, 0, y - 1, z), rn = grid_index(N, 0, y + 1, z);
-  const int64_t rb = grid_index(N, 0, y, z - 1), rbn = grid_index(N, 0, y + 1, z - 1);
-  const int64_t rt = grid_index(N, 0, y, z + 1), rts = grid_index(N, 0, y - 1, z + 1);
+  const int64_t r0 = R.r0, rs = R.rs, rn = R.rn, rb = R.rb, rbn = R.rbn, rt = R.rt, rts = R.rts;
   TR xv[15];
   xv[0] = (TR)xv_[r0 + x - 1];
   xv[1] = (TR)xv_[rs + x];
@@ -748,10 +756,13 @@ __global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__
     const int j = warp + 8 * m, y = Y + j;
     const int x = s0 + lane - 2 * j;
     TR r = 0;
-    if (y >= 1 && y <= N - 2 - z && x >= 1 && x <= N - 1 - y - z) {
-      if (MODE == 0) r = var ? residual_at<TX, TR, true>(t, N, x, y, z, xv, b) : residual_at<TX, TR, false>(t, N, x, y, z, xv, b);
-      else r = (TR)xv[grid_index(N, x, y, z)];
-      acc2 += (double)r * (double)r;
+    if (y >= 1 && y <= N - 2 - z) {  // warp-uniform: the row's starts once per row
+      const RowStarts R = row_starts(N, y, z);
+      if (x >= 1 && x <= N - 1 - y - z) {
+        if (MODE == 0) r = var ? residual_at<TX, TR, true>(t, R, x, xv, b) : residual_at<TX, TR, false>(t, R, x, xv, b);
+        else r = (TR)xv[R.r0 + x];
+        acc2 += (double)r * (double)r;
+      }
     }
     T[lane][j] = (float)r;
   }
@@ -808,9 +819,9 @@ __global__ void __launch_bounds__(256) band_update_kernel(const DevTet *__restri
   for (int m = 0; m < 4; ++m) {
     const int j = warp + 8 * m, y = Y + j;
     const int x = s0 + lane - 2 * j;
-    if (y >= 1 && y <= N - 2 - z && x >= 1 && x <= N - 1 - y - z) {
-      const int64_t gi = grid_index(N, x, y, z);
-      xv[gi] = xv[gi] + (TX)T[lane][j];
+    if (y >= 1 && y <= N - 2 - z) {
+      const int64_t r0 = grid_index(N, 0, y, z);
+      if (x >= 1 && x <= N - 1 - y - z) xv[r0 + x] = xv[r0 + x] + (TX)T[lane][j];
     }
   }
 }

@@ -467,6 +467,15 @@ def main():
                 "traffic": profiled_traffic(dom), "kernel": f"{dom}_kernel", "peak_source": src,
                 "algorithmic_bytes": alg[dom]["bytes"]}
     roof["kernel_ms_per_launch"] = {nm: round(v, 5) for nm, v in per_launch.items()}
+    # The substitutions are bound by their dependency depth (3N - 11
+    # hyperplanes, each a step of the slab on the critical path), not by HBM:
+    # report the measured time per hyperplane beside the HBM fraction.
+    levels = 3 * 2 ** LEVEL - 11
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    sub_ms = (per_launch["forward"] + per_launch["backward"]) / 2
+    depth = {"levels_per_substitution": levels, "us_per_level": round(1e3 * sub_ms / levels, 4),
+             "cycles_per_level": round(sub_ms * 1e-3 / levels * sm_mhz * 1e6),
+             "hbm_time_us_per_substitution": round(1e6 * alg["backward"]["bytes"] / (hbm * 1e9), 2)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -477,6 +486,7 @@ def main():
                     "d2h_bytes_per_step": nn * 8},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "depth": depth,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

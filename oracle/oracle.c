@@ -406,6 +406,71 @@ done:
   return rc;
 }
 
+/* Symmetric Gauss-Seidel as an L D L^T preconditioner, the comparison
+ * smoother of Sec. 4.2: with E the strictly lower part of A_tt in the
+ * lexicographic order and D its diagonal, C = (D + E) D^{-1} (D + E^T) has the
+ * unit-lower factor I + E D^{-1}, i.e. L^p_d = A(p, p+d) / A(p+d, p+d) (0 where
+ * p+d is not interior), and the pivots D^p = A(p, p).
+ * Out (interior order): L[d*nint+i] for d in D_l and D[i]. */
+int orc_sgs_factors(int N, const long *rowptr, const long *col, const double *val, double *Lout, double *Dout) {
+  long nn = orc_num_nodes(N);
+  long *intid = (long *)malloc(sizeof(long) * nn);
+  int *xyz = (int *)malloc(sizeof(int) * 3 * nn);
+  long *rt = row_table(N);
+  if (!intid || !xyz || !rt) { free(intid); free(xyz); free(rt); return ORC_ERR; }
+  long nint = orc_interior_ids(N, intid);
+  orc_coords(N, xyz);
+  double *diag = (double *)malloc(sizeof(double) * nn);
+  if (!diag) { free(intid); free(xyz); free(rt); return ORC_ERR; }
+  for (long g = 0; g < nn; ++g) {
+    diag[g] = 0.0;
+    for (long m = rowptr[g]; m < rowptr[g + 1]; ++m)
+      if (col[m] == g) diag[g] = val[m];
+  }
+  for (long g = 0; g < nn; ++g) {
+    long i = intid[g];
+    if (i < 0) continue;
+    int x = xyz[3 * g], y = xyz[3 * g + 1], z = xyz[3 * g + 2];
+    Dout[i] = diag[g];
+    for (int d = 0; d < 7; ++d) {
+      int qx = x + DIR[d][0], qy = y + DIR[d][1], qz = z + DIR[d][2];
+      double v = 0.0;
+      if (orc_in_interior(N, qx, qy, qz)) {
+        long q = IDX(rt, N, qx, qy, qz);
+        for (long m = rowptr[g]; m < rowptr[g + 1]; ++m)
+          if (col[m] == q) v = val[m] / diag[q];
+      }
+      Lout[(long)d * nint + i] = v;
+    }
+  }
+  free(intid); free(xyz); free(rt); free(diag);
+  return ORC_OK;
+}
+
+/* One symmetric Gauss-Seidel sweep written out directly: over the interior
+ * points in lexicographic order x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii
+ * with the newest values, then the same in reverse order.  Boundary entries
+ * of x are Dirichlet data and are not changed. */
+int orc_sgs_sweep(int N, const long *rowptr, const long *col, const double *val, double *x, const double *b) {
+  long nn = orc_num_nodes(N);
+  long *intid = (long *)malloc(sizeof(long) * nn);
+  if (!intid) return ORC_ERR;
+  orc_interior_ids(N, intid);
+  for (int pass = 0; pass < 2; ++pass)
+    for (long k = 0; k < nn; ++k) {
+      long g = pass == 0 ? k : nn - 1 - k;
+      if (intid[g] < 0) continue;
+      double s = b[g], a = 0.0;
+      for (long m = rowptr[g]; m < rowptr[g + 1]; ++m) {
+        if (col[m] == g) a = val[m];
+        else s -= val[m] * x[col[m]];
+      }
+      x[g] = s / a;
+    }
+  free(intid);
+  return ORC_OK;
+}
+
 /* ---------------------------------------------------------- Alg. 1 ---- */
 
 /* Memory-efficient in-place LDL^T factorisation of Algorithm 1 (Sec. 4.1),

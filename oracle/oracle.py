@@ -50,6 +50,8 @@ def lib():
         L.orc_local_stencil.argtypes = [i, vp, i, d, d, i, i, i, i, vp]
         L.orc_interior_ids.restype = l; L.orc_interior_ids.argtypes = [i, vp]
         L.orc_ilu0.argtypes = [i, vp, vp, vp, vp, vp]
+        L.orc_sgs_factors.argtypes = [i, vp, vp, vp, vp, vp]
+        L.orc_sgs_sweep.argtypes = [i, vp, vp, vp, vp, vp]
         L.orc_alg1.argtypes = [i, vp, i, d, d, i, vp, vp]
         L.orc_surrogate_eval.restype = d; L.orc_surrogate_eval.argtypes = [i, vp, vp, d, d, d]
         L.orc_basis_rows.argtypes = [i, vp, l, vp, vp]
@@ -169,6 +171,28 @@ def ilu0(A, N):
     if rc != 0:
         raise RuntimeError("oracle ILU(0): non-positive pivot")
     return L, D
+
+
+def sgs_factors(A, N):
+    """Symmetric Gauss-Seidel in the L D L^T form of the smoother:
+    (L[7, nint], D[nint]) with L^p_d = A(p, p+d) / A(p+d, p+d), D^p = A(p, p)."""
+    rowptr, col, val = A
+    _, nint = interior_ids(N)
+    L = np.zeros((7, nint)); D = np.zeros(nint)
+    if lib().orc_sgs_factors(N, _p(rowptr), _p(col), _p(val), _p(L), _p(D)) != 0:
+        raise RuntimeError("oracle SGS factors failed")
+    return L, D
+
+
+def sgs_sweep(A, N, x, b):
+    """One textbook symmetric Gauss-Seidel sweep (forward then backward),
+    in place on x."""
+    rowptr, col, val = A
+    assert x.dtype == np.float64 and x.flags.c_contiguous
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    if lib().orc_sgs_sweep(N, _p(rowptr), _p(col), _p(val), _p(x), _p(bb)) != 0:
+        raise RuntimeError("oracle SGS sweep failed")
+    return x
 
 
 def alg1(P, N, coeff=None):
@@ -316,12 +340,15 @@ class Problem:
     """Everything the oracle knows about one macro-tetrahedron at one level:
     the assembled matrix, the exact ILU(0) and (optionally) the surrogate fit."""
 
-    def __init__(self, P, level, coeff=None, deg=None, sample_level=None, ridge=1e-6, use_alg1=False):
+    def __init__(self, P, level, coeff=None, deg=None, sample_level=None, ridge=1e-6, use_alg1=False,
+                 factor="ilu"):
         self.P = np.ascontiguousarray(P, dtype=np.float64).reshape(4, 3)
         self.level, self.N = level, 2 ** level
         self.coeff = coeff or Coeff()
         self.A = assemble(self.P, self.N, self.coeff)
-        if use_alg1:
+        if factor == "sgs":
+            self.L, self.D = sgs_factors(self.A, self.N)
+        elif use_alg1:
             self.L, self.D = alg1(self.P, self.N, self.coeff)
         else:
             self.L, self.D = ilu0(self.A, self.N)

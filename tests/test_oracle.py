@@ -467,3 +467,53 @@ def test_outer_solves_reach_tolerance(orc):
     assert it2 < it1
     for x in (x1, x2):
         assert np.abs(x - xref).max() < 1e-6 * np.abs(xref).max()
+
+
+# ------------------------------------------- symmetric Gauss-Seidel (Sec. 4.2)
+
+@pytest.mark.parametrize("level,kind", [(3, "const"), (4, "sinprod")])
+def test_sgs_factor_form_is_textbook_sgs(orc, level, kind):
+    """The L D L^T form of the comparison smoother (L^p_d = a(p,p+d)/a(p+d,p+d),
+    D^p = a(p,p)) applied by Algorithm 2 equals a symmetric Gauss-Seidel
+    sweep written out point by point."""
+    N = 2 ** level
+    co = {"const": orc.Coeff(), "sinprod": orc.Coeff("sinprod", 1.0, 0.5)}[kind]
+    pr = orc.Problem(si.macro_tet(60), level, co, factor="sgs")
+    x0 = si.boundary_data(level, 61)
+    b = si.rhs(level, 62)
+    xa = orc.smooth(pr.A, N, pr.L, 1.0 / pr.D, x0.copy(), b, 2)
+    xb = x0.copy()
+    for _ in range(2):
+        orc.sgs_sweep(pr.A, N, xb, b)
+    assert np.abs(xa - xb).max() < 1e-12 * np.abs(xb).max()
+
+
+def test_sgs_factors_reproduce_the_splitting(orc):
+    """L D L^T of the SGS factors is (D + E) D^{-1} (D + E^T), with D and E the
+    diagonal and strictly lower part of the interior block (dense algebra)."""
+    level, N = 3, 8
+    pr = orc.Problem(si.macro_tet(63), level, orc.Coeff("kappa_i", 0.0, 0.0, 2), factor="sgs")
+    Att = interior_block(orc, pr.A, N)
+    Dm = np.diag(np.diag(Att))
+    E = np.tril(Att, -1)
+    want = (Dm + E) @ np.linalg.inv(Dm) @ (Dm + E).T
+    Lm = lower_matrix(orc, N, pr.L)
+    got = Lm @ np.diag(pr.D) @ Lm.T
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_exact_ilu_beats_sgs(orc):
+    """With exact factors the ILU(0) smoother contracts faster than symmetric
+    Gauss-Seidel on the same problem (the comparison of Sec. 4.2)."""
+    level, N = 4, 16
+    P = si.macro_tet(64)
+    ilu = orc.Problem(P, level)
+    sgs = orc.Problem(P, level, factor="sgs")
+    Att = interior_block(orc, ilu.A, N)
+    rho = []
+    for pr in (ilu, sgs):
+        Lm = lower_matrix(orc, N, pr.L)
+        C = Lm @ np.diag(pr.D) @ Lm.T
+        ev = np.linalg.eigvals(np.eye(len(Att)) - np.linalg.solve(C, Att))
+        rho.append(np.abs(ev).max())
+    assert rho[0] < rho[1] < 1

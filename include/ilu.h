@@ -79,7 +79,16 @@ typedef struct {
   int device;          /* CUDA device ordinal; -1: host-only handle (setup only) */
   long long max_wait_spins; /* bound on device-side spin waits; <=0: default */
   int kernel;          /* substitution kernels of FP32/MIXED sweeps: an ilu_kernel value */
+  int factor;          /* factors the surrogates approximate: an ilu_factor value */
 } ilu_opts;
+
+/* Which L D L^T preconditioner the surrogates approximate (Sec. 4.2):
+ *   ILU_FACTOR_ILU0  exact ILU(0) of the interior block, by Alg. 1 (default);
+ *   ILU_FACTOR_SGS   symmetric Gauss-Seidel, the paper's comparison smoother:
+ *                    L^p_d = A^p_d / A^{p+d}_c, D^p = A^p_c, i.e. the
+ *                    factors of (D + E) D^-1 (D + E^T).
+ * Sampling, fit, tables and sweeps are the same for both. */
+typedef enum { ILU_FACTOR_ILU0 = 0, ILU_FACTOR_SGS = 1 } ilu_factor;
 
 /* Substitution kernels of the FP32/MIXED sweeps.  Both run the same
  * arithmetic (Alg. 2, V2) and agree to rounding; they differ in how the

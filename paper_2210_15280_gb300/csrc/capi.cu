@@ -571,6 +571,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->device = 0;
   o->max_wait_spins = 0;
   o->kernel = ILU_KERNEL_AUTO;
+  o->factor = ILU_FACTOR_ILU0;
   return ILU_OK;
 }
 
@@ -604,6 +605,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (opts) o = *opts;
   if (o.precision < 0 || o.precision > 2) return fail(ILU_EINVAL, "unknown precision");
   if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_BAND) return fail(ILU_EINVAL, "unknown kernel choice");
+  if (o.factor != ILU_FACTOR_ILU0 && o.factor != ILU_FACTOR_SGS) return fail(ILU_EINVAL, "unknown factor choice");
   int deg[3];
   for (int c = 0; c < 3; ++c) deg[c] = o.deg[c] >= 0 ? o.deg[c] : poly_degree;
   ilu_tet t = new (std::nothrow) ilu_tet_s;
@@ -614,6 +616,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   std::string err;
   ilu_status st;
   try {
+    t->host.factor = o.factor;
     st = host_setup(t->host, macro_tet, level, coeff, deg, o.sample_level, o.ridge, err);
   } catch (const std::bad_alloc &) {
     st = ILU_ENOMEM;

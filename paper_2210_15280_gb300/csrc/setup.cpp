@@ -390,20 +390,25 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
           const std::vector<double> &buf = dir_dz(d) < 0 ? prv : cur;
           nb[d] = &buf[((size_t)(y + dir_dy(d)) * S + (x + dir_dx(d))) * 8];
         }
+        // symmetric Gauss-Seidel keeps the first term of each recursion: the
+        // neighbour's stored pivot is then its diagonal entry a(p+d, p+d)
+        const bool ilu = t.factor == ILU_FACTOR_ILU0;
         double Lp[7];
         for (int k = 0; k < 7; ++k) {
           const int d = pl.order[k];
           double v = A[d];
-          for (int m = 0; m < pl.nterm[d]; ++m) {
-            const int e = pl.e[d][m];
-            v -= Lp[e] * nb[e][7] * nb[d][pl.f[d][m]];
-          }
+          if (ilu)
+            for (int m = 0; m < pl.nterm[d]; ++m) {
+              const int e = pl.e[d][m];
+              v -= Lp[e] * nb[e][7] * nb[d][pl.f[d][m]];
+            }
           Lp[d] = v / nb[d][7];
         }
         double Dp = A[kCentre];
-        for (int d = 0; d < 7; ++d) Dp -= Lp[d] * Lp[d] * nb[d][7];
+        if (ilu)
+          for (int d = 0; d < 7; ++d) Dp -= Lp[d] * Lp[d] * nb[d][7];
         if (!(Dp > 0.0)) {
-          err = "non-positive ILU(0) pivot";
+          err = ilu ? "non-positive ILU(0) pivot" : "non-positive diagonal entry";
           return ILU_ESINGULAR;
         }
         double *me = &cur[((size_t)y * S + x) * 8];

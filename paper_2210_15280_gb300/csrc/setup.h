@@ -19,6 +19,7 @@ struct HostTet {
   int M = 1;            // (dgx+1)(dgy+1)(dgz+1)
   int LH = 5;           // sampling level
   double ridge = 1e-6;  // relative Tikhonov weight
+  int factor = 0;       // ilu_factor: ILU(0) (Alg. 1) or symmetric Gauss-Seidel
   bool const_kappa = true;
   double Kunit[6][4][4] = {};  // unit-coefficient element matrices of the six micro-tet classes
   int off[6][4][3] = {};       // their vertex offsets

@@ -189,3 +189,27 @@ def test_library_fit_end_to_end(g, orc):
     xd = dev(x0, torch.float64)
     t.smooth(xd, dev(b, torch.float64), 1)
     assert rel(xd.cpu().numpy(), xo) < 1e-5
+
+
+@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND"), ("F32", "BAND")])
+def test_sgs_smoother_matches_oracle(g, orc, prec, kernel):
+    """The symmetric Gauss-Seidel comparison smoother (ilu_opts.factor = SGS)
+    runs through the same surrogate pipeline and kernels."""
+    level, deg = 5, 4
+    P = si.macro_tet(66)
+    co = ("sinprod", 1.0, 0.5, 0)
+    N = 2 ** level
+    pr = orc.Problem(P, level, orc.Coeff(*co), deg=deg, factor="sgs")
+    p = getattr(g, prec)
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=p,
+              kernel=getattr(g, "KERNEL_" + kernel), factor=g.FACTOR_SGS)
+    t.import_surrogate(pr.coefs)
+    dt = torch.float32 if p == g.F32 else torch.float64
+    x = si.boundary_data(level, 67)
+    b = si.rhs(level, 68)
+    Ls, Dinv = pr.surrogate_factors()
+    xo = orc.smooth(pr.A, N, Ls, Dinv, x.copy(), b, 1)
+    xd = dev(x, dt)
+    t.smooth(xd, dev(b, dt), 1)
+    tol = 1e-12 if p == g.F64 else 1e-5
+    assert rel(xd.cpu().numpy().astype(np.float64), xo) < tol

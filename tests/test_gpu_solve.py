@@ -85,3 +85,24 @@ def test_solve_reports_nonconvergence(g):
     x = torch.zeros_like(b)
     it, rel, ok = t.solve(x, b, g.RICHARDSON, 1e-12, 3)
     assert not ok and it == 3 and rel > 1e-12
+
+
+@pytest.mark.parametrize("method", ["RICHARDSON", "PCG"])
+def test_ilu_smoother_beats_sgs(g, orc, method):
+    """The comparison of Sec. 4.2 on one macro-tet: the surrogate ILU(0)
+    smoother needs fewer iterations than surrogate symmetric Gauss-Seidel,
+    and both reach the same solution."""
+    level = 5
+    P = si.macro_tet(108)
+    co = g.make_coeff("sinprod", 1.0, 0.5)
+    b = torch.tensor(si.rhs(level, 109), dtype=torch.float64, device="cuda")
+    res = {}
+    for name, factor in [("ilu", g.FACTOR_ILU0), ("sgs", g.FACTOR_SGS)]:
+        t = g.Tet(P, level, coeff=co, poly_degree=4, precision=g.MIXED, factor=factor)
+        x = torch.zeros_like(b)
+        it, rel, ok = t.solve(x, b, getattr(g, method), 1e-8, 20000)
+        assert ok and rel < 1e-8
+        res[name] = (it, x.cpu().numpy())
+    assert res["ilu"][0] < res["sgs"][0]
+    a, c = res["ilu"][1], res["sgs"][1]
+    assert np.abs(a - c).max() < 1e-6 * np.abs(a).max()

@@ -131,3 +131,31 @@ def test_invalid_inputs_raise(g):
         t.import_surrogate(np.zeros(5))
     with pytest.raises(g.IluError):
         t.eval_surrogate(0, 1, 1)
+
+
+@pytest.mark.parametrize("level,kind", [(3, "const"), (4, "sinprod")])
+def test_sgs_factors_match_oracle(g, orc, level, kind):
+    """With ilu_opts.factor = SGS the library's exact factors are the
+    symmetric Gauss-Seidel ones (a(p,p+d)/a(p+d,p+d) and a(p,p))."""
+    N = 2 ** level
+    P = si.macro_tet(34)
+    co = ("sinprod", 1.0, 0.5, 0) if kind == "sinprod" else ("const", 1.0, 0.0, 0)
+    t = host_tet(g, P, level, coeff=g.make_coeff(*co), deg=2, factor=g.FACTOR_SGS)
+    A = orc.assemble(P, N, orc.Coeff(*co))
+    L, D = orc.sgs_factors(A, N)
+    got = np.array([t.exact_factor(*p) for p in orc.interior_coords(N)])
+    assert np.abs(got[:, :7] - L.T).max() < 1e-13
+    assert np.abs(got[:, 7] - D).max() < 1e-13 * D.max()
+
+
+def test_sgs_surrogate_matches_oracle_fit(g, orc):
+    level, deg, N = 5, 4, 32
+    P = si.macro_tet(35)
+    co = ("sinprod", 1.0, 0.5, 0)
+    t = host_tet(g, P, level, coeff=g.make_coeff(*co), deg=deg, factor=g.FACTOR_SGS)
+    pr = orc.Problem(P, level, orc.Coeff(*co), deg=deg, factor="sgs")
+    Ls, Dinv = pr.surrogate_factors()
+    ic = orc.interior_coords(N)
+    got = np.array([t.eval_surrogate(*p) for p in ic[::5]])
+    assert np.abs(got[:, :7] - Ls.T[::5]).max() < 1e-8
+    assert np.abs(got[:, 7] - Dinv[::5]).max() < 1e-8 * np.abs(Dinv).max()

@@ -25,6 +25,13 @@ Further workloads print a line of the same form (not the default run):
                      (Richardson) or 5-8 (--method pcg), mixed coefficients,
                      to 1e-8; solves/s and p50/p99 latency, beside the same
                      requests solved one after another with FP64 sweeps.
+  --workload smoothers  iteration counts of the surrogate ILU(0) smoother
+                     against the surrogate symmetric Gauss-Seidel smoother,
+                     both as Richardson smoothers and as CG preconditioners,
+                     to a relative residual of 1e-8: on the default level-7
+                     tet, on macro-tets of the mesh above (level 6), and on
+                     trirectangular tets whose top vertex sinks to height h
+                     (level 6, all 24 vertex orders for ILU).
 """
 import argparse
 import json
@@ -366,6 +373,63 @@ def serve_workload(args, g, torch):
             "e2e": {"value": nreq / wall, "unit": "solves/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None}}
 
 
+def smoothers_workload(args, g, torch):
+    """Iterations to a relative residual of 1e-8 for ILU(0) and SGS surrogates
+    on the same tets; log(rho_ILU)/log(rho_SGS) = it_SGS/it_ILU for Richardson
+    (the measure of the height sweep of Sec. 4.2, here for the single-level
+    smoother)."""
+    import itertools
+    t_start = time.time()
+    rtol, cap = 1e-8, 20000
+    co = g.make_coeff(*COEFF[:3])
+
+    def iters(P, level, deg, method, factor, coeff=co, seed=RHS_SEED, limit=cap):
+        try:
+            t = g.Tet(P, level, coeff=coeff, poly_degree=deg, precision=g.MIXED, factor=factor)
+        except g.IluError as e:
+            return {"error": str(e)}
+        b = torch.tensor(si.rhs(level, seed), dtype=torch.float64, device="cuda")
+        x = torch.zeros_like(b)
+        it, rel, ok = t.solve(x, b, method, rtol, limit)
+        t.close()
+        return it if ok else {"not_converged": it, "rel": rel}
+
+    def pair(P, level, deg, coeff=co):
+        out = {}
+        for mname, m in [("richardson", g.RICHARDSON), ("pcg", g.PCG)]:
+            for fname, f in [("ilu", g.FACTOR_ILU0), ("sgs", g.FACTOR_SGS)]:
+                out[f"{mname}_{fname}"] = iters(P, level, deg, m, f, coeff)
+        return out
+
+    c2 = pair(si.macro_tet(TET_SEED), LEVEL, DEG)
+    mesh = [pair(P, 6, 5, g.make_coeff("const")) for P in si.macro_mesh(6)[:4]]
+    heights = []
+    for h in [1.0, 0.5, 0.25, 0.125, 0.0625]:
+        P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, h]], float)
+        row = {"h": h}
+        row.update(pair(P, 6, 6, g.make_coeff("const")))
+        best = None
+        for perm in itertools.permutations(range(4)):
+            it = iters(P[list(perm)], 6, 6, g.RICHARDSON, g.FACTOR_ILU0, g.make_coeff("const"),
+                       limit=best[0] if best else cap)
+            if isinstance(it, int) and (best is None or it < best[0]):
+                best = (it, list(perm))
+        row["richardson_ilu_best_order"] = best
+        sg = row["richardson_sgs"]
+        if best and isinstance(sg, int):
+            row["log_rho_ratio_best"] = sg / best[0]
+        heights.append(row)
+    ri, rs = c2["richardson_ilu"], c2["richardson_sgs"]
+    return {"metric": "Richardson iterations to relative residual 1e-8, surrogate ILU(0) smoother",
+            "value": ri, "unit": "iterations", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": (time.time() - t_start) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", Richardson and PCG to 1e-8 from x0 = 0, ILU(0) and SGS",
+                       "precision": "MIXED", "parallelism": "replicas x1"},
+            "sgs_value": rs, "ratio_sgs_over_ilu": (rs / ri) if isinstance(ri, int) and isinstance(rs, int) else None,
+            "l7_tet": c2, "mesh_tets_l6_deg5_kappa1": mesh, "trirectangular_l6_deg6_kappa1": heights}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +437,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg"])
     ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
@@ -388,7 +452,8 @@ def main():
     torch.cuda.set_device(local)
     if args.workload != "single":
         if rank == 0:
-            line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload}[args.workload](
+            line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload,
+                    "smoothers": smoothers_workload}[args.workload](
                 args, g, torch)
             print(json.dumps(line), flush=True)
         return

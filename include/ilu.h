@@ -231,6 +231,58 @@ ilu_status ilu_batch_destroy(ilu_batch b);
  * Results equal ilu_smooth on each tet, bit for bit. */
 ilu_status ilu_batch_smooth(ilu_batch bt, void *const *x, const void *const *b, int sweeps, void *stream);
 
+/* ------------------------------------------------------------- multigrid -- */
+
+/* Geometric multigrid on one macro-tetrahedron (Sec. 4.2 numerical results):
+ * the nested lattices of levels 2..level, a V-cycle with nu pre- and nu
+ * post-smoothing sweeps of Alg. 2 on every level above 2 and an exact solve
+ * on level 2, whose one interior point is solved by division.
+ *   - Smoother: one surrogate handle per level 3..level, set up as
+ *     ilu_setup(macro_tet, l, coeff, poly_degree, opts) would; opts (nullable)
+ *     selects precision, kernel and factor (ILU(0), or the symmetric
+ *     Gauss-Seidel comparison smoother) for all levels.
+ *   - Grid transfer: prolongation is the coarse piecewise-linear function
+ *     evaluated at the fine points (a fine point with all coordinates even
+ *     takes the coarse value; any other is the midpoint 2c + d of the coarse
+ *     edge (c, c + d), d in D, and takes the mean of the two end values).
+ *     Restriction is its transpose: b_c = r(2c) + (1/2) sum_{d in D} r(2c + d).
+ *     Coarse operators are those of the coarse lattices, which equal the
+ *     Galerkin products for constant kappa.
+ * level in [3, 10], nu in [1, 16].  The handle owns one vector triple per
+ * level (x, b, r in the vector type) and the level handles.  Errors as for
+ * ilu_setup; ILU_EINVAL also for nu or level out of range.  The paper's
+ * outer solvers (Steklov-Poincare iterations over macro-tets) are not part
+ * of this library. */
+typedef struct ilu_mg_s *ilu_mg;
+ilu_status ilu_mg_setup(const double macro_tet[12], int level, const ilu_coeff *coeff, int poly_degree, int nu,
+                        const ilu_opts *opts, ilu_mg *out);
+ilu_status ilu_mg_destroy(ilu_mg mg);
+
+/* Borrow the smoother handle of one level (3..finest), e.g. to export or
+ * import its surrogate.  It stays owned by mg; do not destroy it. */
+ilu_status ilu_mg_level(ilu_mg mg, int level, ilu_tet *out);
+
+/* `cycles` V-cycles for A x = b on the finest level: x (in/out) and b as for
+ * ilu_smooth.  res_norms (host, nullable, length cycles) receives ||b - A x||_2
+ * over the interior after each cycle and makes the call synchronous. */
+ilu_status ilu_mg_cycle(ilu_mg mg, void *x, const void *b, int cycles, void *stream, double *res_norms);
+
+/* Solve A x = b to ||b - A x||_2 <= rtol ||b||_2 by V-cycle iteration
+ * (ILU_RICHARDSON: x <- x + V(b - A x)) or by CG preconditioned with one
+ * V-cycle from zero (ILU_PCG; symmetric since the smoother is symmetric, pre
+ * and post counts are equal and restriction is the transposed prolongation).
+ * Synchronous; ILU_ENOTCONV at max_iter. */
+ilu_status ilu_mg_solve(ilu_mg mg, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
+                        int *iters, double *rel_res);
+
+/* Asymptotic convergence factor of the V-cycle (Sec. 4.2): a power iteration
+ * of `steps` cycles on the error propagation operator (b = 0) from the start
+ * error e (device, full grid, boundary entries 0; overwritten), normalised
+ * after every cycle.  rho (host) receives the last ratio of successive
+ * interior norms; history (host, nullable, length steps) all of them.
+ * Synchronous. */
+ilu_status ilu_mg_rate(ilu_mg mg, void *e, int steps, void *stream, double *rho, double *history);
+
 /* ----------------------------------------------------------- request loop -- */
 
 typedef struct {

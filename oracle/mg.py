@@ -67,11 +67,14 @@ def prolongation(Nc):
 
 
 class Level:
-    def __init__(self, P, level, coeff, smoother):
+    def __init__(self, P, level, coeff, smoother, factors=None):
         self.level, self.N = level, 2 ** level
         self.A = orc.assemble(P, self.N, coeff)
         ids, self.nint = orc.interior_ids(self.N)
         self.inner = np.nonzero(ids >= 0)[0]
+        if factors is not None:  # given (L[7, nint], D^-1[nint]), e.g. surrogate values
+            self.L, self.Dinv = factors
+            return
         if smoother == "ilu":
             L, D = orc.ilu0(self.A, self.N)
         elif smoother == "sgs":
@@ -83,13 +86,16 @@ class Level:
 
 class Hierarchy:
     """Levels coarsest..finest of one macro-tet with the given smoother and
-    nu_pre = nu_post smoothing steps of the V-cycle."""
+    nu_pre = nu_post smoothing steps of the V-cycle.  `factors` (optional)
+    maps a level to the (L, D^-1) its smoother uses instead of the exact
+    factors, e.g. the values of surrogate polynomials."""
 
-    def __init__(self, P, finest, coarsest=2, coeff=None, smoother="ilu", nu=3):
+    def __init__(self, P, finest, coarsest=2, coeff=None, smoother="ilu", nu=3, factors=None):
         P = np.ascontiguousarray(P, dtype=np.float64).reshape(4, 3)
         coeff = coeff or orc.Coeff()
+        factors = factors or {}
         self.nu, self.coarsest, self.finest = nu, coarsest, finest
-        self.lv = {l: Level(P, l, coeff, smoother) for l in range(coarsest, finest + 1)}
+        self.lv = {l: Level(P, l, coeff, smoother, factors.get(l)) for l in range(coarsest, finest + 1)}
         # interior-to-interior transfers (the correction vanishes on the boundary)
         self.Pm = {}
         for l in range(coarsest + 1, finest + 1):

@@ -33,6 +33,7 @@ EXPORTS = [
     "ilu_batch_smooth", "ilu_server_create", "ilu_server_submit", "ilu_server_wait", "ilu_server_release",
     "ilu_server_stats", "ilu_server_destroy", "ilu_num_nodes", "ilu_num_interior", "ilu_index",
     "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read", "ilu_residual_noalloc",
+    "ilu_mg_setup", "ilu_mg_destroy", "ilu_mg_level", "ilu_mg_cycle", "ilu_mg_solve", "ilu_mg_rate",
 ]
 
 
@@ -111,6 +112,12 @@ def lib():
         L.ilu_server_release.argtypes = [vp, ctypes.c_uint64]
         L.ilu_server_stats.argtypes = [vp, P(Stats)]
         L.ilu_server_destroy.argtypes = [vp]
+        L.ilu_mg_setup.argtypes = [P(ctypes.c_double * 12), i, P(Coeff), i, i, P(Opts), P(vp)]
+        L.ilu_mg_destroy.argtypes = [vp]
+        L.ilu_mg_level.argtypes = [vp, i, P(vp)]
+        L.ilu_mg_cycle.argtypes = [vp, vp, vp, i, vp, vp]
+        L.ilu_mg_solve.argtypes = [vp, vp, vp, i, d, i, vp, vp, vp]
+        L.ilu_mg_rate.argtypes = [vp, vp, i, vp, vp, vp]
         L.ilu_profile_enable.argtypes = [vp, i]
         L.ilu_profile_read.argtypes = [vp, vp, P(ctypes.c_longlong)]
         L.ilu_num_nodes.argtypes = [i]; L.ilu_num_nodes.restype = sz
@@ -285,6 +292,72 @@ class Tet:
         out = np.zeros(15)
         _check(lib().ilu_stencil(self.h, int(x), int(y), int(z), _ptr(out)))
         return out
+
+
+class _Borrowed(Tet):
+    """A level handle owned by a multigrid hierarchy (never destroyed here)."""
+
+    def __init__(self, h, level, precision, owner):
+        self.h, self.level, self.N, self.precision, self._owner = h, level, 2 ** level, precision, owner
+
+    def close(self):
+        self.h = None
+
+
+class Multigrid:
+    """Geometric multigrid V-cycle on one macro-tet, levels 2..level, with the
+    surrogate smoother on levels >= 3 (wraps an ilu_mg handle)."""
+
+    def __init__(self, macro_tet, level, coeff=None, poly_degree=4, nu=3, **opts):
+        P = (ctypes.c_double * 12)(*np.asarray(macro_tet, dtype=np.float64).reshape(12))
+        self.level, self.nu = int(level), int(nu)
+        self.opts = make_opts(**opts)
+        self.precision = self.opts.precision
+        h = ctypes.c_void_p()
+        c = coeff if coeff is not None else make_coeff()
+        _check(lib().ilu_mg_setup(ctypes.byref(P), self.level, ctypes.byref(c), int(poly_degree), self.nu,
+                                  ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ilu_mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tet(self, level):
+        """The smoother handle of one level (owned by the hierarchy)."""
+        h = ctypes.c_void_p()
+        _check(lib().ilu_mg_level(self.h, int(level), ctypes.byref(h)))
+        return _Borrowed(h, int(level), self.precision, self)
+
+    def cycle(self, x, b, cycles=1, stream=None, norms=False):
+        out = np.zeros(max(cycles, 1)) if norms else None
+        _check(lib().ilu_mg_cycle(self.h, _ptr(x), _ptr(b), int(cycles), _stream(stream),
+                                  _ptr(out) if norms else None))
+        return out[:cycles] if norms else None
+
+    def solve(self, x, b, method=RICHARDSON, rtol=1e-8, max_iter=1000, stream=None):
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        st = lib().ilu_mg_solve(self.h, _ptr(x), _ptr(b), int(method), float(rtol), int(max_iter),
+                                _stream(stream), ctypes.byref(it), ctypes.byref(rel))
+        if st not in (ILU_OK, ILU_ENOTCONV):
+            _check(st)
+        return it.value, rel.value, st == ILU_OK
+
+    def rate(self, e, steps=20, stream=None):
+        """(rho, history) of a power iteration from the start error e (device,
+        full grid, boundary 0; overwritten)."""
+        rho = ctypes.c_double(0.0)
+        hist = np.zeros(steps)
+        _check(lib().ilu_mg_rate(self.h, _ptr(e), int(steps), _stream(stream), ctypes.byref(rho), _ptr(hist)))
+        return rho.value, hist
 
 
 class Batch:

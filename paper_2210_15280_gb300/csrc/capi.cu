@@ -557,6 +557,29 @@ bool tet_view(ilu_tet t, TetView *v) {
 WaveGeom wave_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
   return pick_geom(N, kind, dxp, dx, fwd, requested);
 }
+ilu_status tet_sweeps(ilu_tet t, void *x, const void *b, int n, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(t->mu);
+  for (int k = 0; k < n; ++k) {
+    ilu_status st = sweep(t, x, b, nullptr, s);
+    if (st != ILU_OK) {
+      t->failed = true;
+      return st;
+    }
+  }
+  return ILU_OK;
+}
+ilu_status tet_residual(ilu_tet t, const void *x, const void *b, void *r, double *d_norm, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(t->mu);
+  const int vkind = t->precision == ILU_F32 ? kSweepF32 : kSweepF64;
+  int used = 0;
+  CK(launch_residual(t->dev, vkind, x, b, r, t->d_partials, t->nblocks, &used, s), "residual launch");
+  if (d_norm) CK(launch_norm_finish(t->d_partials, used, d_norm, s), "norm launch");
+  return ILU_OK;
+}
+ilu_status tet_check(ilu_tet t, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(t->mu);
+  return read_status(t, s);
+}
 }  // namespace ilu
 
 extern "C" {

@@ -1,0 +1,145 @@
+"""GPU multigrid (ilu_mg_*) against the oracle's V-cycle (oracle/mg.py).
+
+Both sides use the same surrogate polynomials on every smoothed level: the
+oracle fits them, the library imports the coefficients level by level.  One
+V-cycle from the same start vector must agree element by element:
+  * F64: within 1e-12 relative (max abs difference / max abs value),
+  * MIXED and F32: within 1e-5 relative.
+The convergence factors measured on the GPU are then compared with the
+oracle's exact-factor rates, which are pinned to Table 2 of the paper.
+"""
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_15280_gb300 as g
+    g.build()
+    return g
+
+
+@pytest.fixture(scope="module")
+def omg(orc):
+    from oracle import mg
+    return mg
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(v, dt):
+    return torch.tensor(v, dtype=dt, device="cuda")
+
+
+CO = {"const": ("const", 1.0, 0.0, 0), "sinprod": ("sinprod", 1.0, 0.5, 0)}
+
+
+def pair(g, orc, omg, P, level, kind, deg, prec, factor="ilu", nu=3):
+    """GPU hierarchy with the oracle's surrogate fits imported, and the
+    oracle hierarchy using the values of the same polynomials."""
+    co = CO[kind]
+    m = g.Multigrid(P, level, coeff=g.make_coeff(*co), poly_degree=deg, nu=nu, precision=prec,
+                    factor=g.FACTOR_SGS if factor == "sgs" else g.FACTOR_ILU0)
+    fac = {}
+    for l in range(3, level + 1):
+        pr = orc.Problem(P, l, orc.Coeff(*co), deg=deg, factor=factor)
+        m.tet(l).import_surrogate(pr.coefs)
+        fac[l] = pr.surrogate_factors()
+    H = omg.Hierarchy(P, level, coeff=orc.Coeff(*co), nu=nu, factors=fac)
+    return m, H
+
+
+@pytest.mark.parametrize("level,kind,prec", [(3, "const", "F64"), (4, "sinprod", "F64"), (5, "const", "F64"),
+                                             (6, "sinprod", "F64"), (5, "sinprod", "MIXED"),
+                                             (6, "const", "MIXED"), (5, "const", "F32")])
+def test_vcycle_matches_oracle(g, orc, omg, level, kind, prec):
+    P = si.macro_tet(40 + level)
+    m, H = pair(g, orc, omg, P, level, kind, 4, getattr(g, prec))
+    x = si.boundary_data(level, 41)
+    b = si.rhs(level, 42)
+    xo = H.vcycle(level, x.copy(), b)
+    dt = torch.float32 if prec == "F32" else torch.float64
+    xd = dev(x, dt)
+    m.cycle(xd, dev(b, dt), 1)
+    tol = 1e-12 if prec == "F64" else 1e-5
+    assert rel(xd.cpu().numpy().astype(np.float64), xo) < tol
+    m.close()
+
+
+def test_sgs_vcycle_matches_oracle(g, orc, omg):
+    level = 5
+    P = si.macro_tet(47)
+    m, H = pair(g, orc, omg, P, level, "const", 4, g.F64, factor="sgs")
+    x = si.boundary_data(level, 48)
+    b = si.rhs(level, 49)
+    xo = H.vcycle(level, x.copy(), b)
+    xd = dev(x, torch.float64)
+    m.cycle(xd, dev(b, torch.float64), 1)
+    assert rel(xd.cpu().numpy(), xo) < 1e-12
+
+
+def test_three_cycles_and_norms(g, orc, omg):
+    """Several cycles in one call, with the residual norms it reports."""
+    level = 5
+    P = si.macro_tet(50)
+    m, H = pair(g, orc, omg, P, level, "sinprod", 4, g.F64)
+    x = si.boundary_data(level, 51)
+    b = si.rhs(level, 52)
+    xo = x.copy()
+    ref = []
+    for _ in range(3):
+        H.vcycle(level, xo, b)
+        ref.append(orc.residual(H.lv[level].A, H.lv[level].N, xo, b)[1])
+    xd = dev(x, torch.float64)
+    norms = m.cycle(xd, dev(b, torch.float64), 3, norms=True)
+    assert rel(xd.cpu().numpy(), xo) < 1e-11
+    assert np.allclose(norms, ref, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("method", ["RICHARDSON", "PCG"])
+@pytest.mark.parametrize("prec", ["F64", "MIXED"])
+def test_mg_solve_is_level_independent(g, method, prec):
+    """With the V-cycle the iteration count stays flat as the level grows
+    (the surrogate ILU smoother alone needs about 4x more per level)."""
+    counts = []
+    for level in [5, 6, 7]:
+        m = g.Multigrid(si.macro_tet(3), level, coeff=g.make_coeff("sinprod", 1.0, 0.5), poly_degree=6, nu=3,
+                        precision=getattr(g, prec))
+        b = dev(si.rhs(level, 4), torch.float64)
+        x = torch.zeros_like(b)
+        it, r, ok = m.solve(x, b, getattr(g, method), 1e-8, 100)
+        assert ok and r <= 1e-8
+        counts.append(it)
+        m.close()
+    assert max(counts) <= 12 and max(counts) - min(counts) <= 2, counts
+
+
+def test_rate_matches_oracle_exact_rates(g, orc, omg):
+    """rho of the GPU V-cycle with degree-6 surrogates on the regular tet
+    and two Cap orders, beside the oracle's exact-ILU rates (which match
+    Table 2): the surrogate changes rho by a few per cent at most."""
+    reg = np.array([[0, 0, 0], [1, 0, 0], [0.5, np.sqrt(3) / 2, 0], [0.5, np.sqrt(3) / 6, np.sqrt(2 / 3)]])
+    cap = np.array([[0, 0, 0], [1, 0, 0], [0.5, 0.866, 0], [0.5, 0.288, 0.093]])
+    cap_1243 = cap[[0, 1, 3, 2]]
+    level = 6
+    _, nint = orc.interior_ids(64)
+    e0 = np.random.default_rng(5).uniform(-1, 1, nint)
+    ids, _ = orc.interior_ids(64)
+    full = np.zeros(orc.num_nodes(64))
+    full[ids >= 0] = e0
+    for P, lo, hi in [(reg, 0.02, 0.03), (cap, 0.005, 0.02), (cap_1243, 0.40, 0.46)]:
+        ro, _ = omg.Hierarchy(P, level).rate(e0)
+        m = g.Multigrid(P, level, poly_degree=6, nu=3, precision=g.F64)
+        rg, hist = m.rate(dev(full, torch.float64))
+        m.close()
+        assert lo <= ro <= hi and lo <= rg <= hi, (ro, rg)

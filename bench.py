@@ -32,6 +32,11 @@ Further workloads print a line of the same form (not the default run):
                      tet, on macro-tets of the mesh above (level 6), and on
                      trirectangular tets whose top vertex sinks to height h
                      (level 6, all 24 vertex orders for ILU).
+  --workload mg      geometric multigrid (V(3,3)-cycle, levels 2..L, exact
+                     solve on level 2) on the default tet: V-cycle time and
+                     solves to 1e-8 by V-cycle iteration and by V-cycle
+                     preconditioned CG at levels 5-9, and the convergence
+                     factors of the paper's Table 2 shapes measured on the GPU.
 """
 import argparse
 import json
@@ -430,6 +435,71 @@ def smoothers_workload(args, g, torch):
             "l7_tet": c2, "mesh_tets_l6_deg5_kappa1": mesh, "trirectangular_l6_deg6_kappa1": heights}
 
 
+TABLE2 = {  # vertex lists of the shapes (Table SM1; Spindle y read as 10) and the printed ILU rates
+    "spindle": ([[0, 0, 0.5], [0, 0, -0.5], [0.5, 10, 0], [-0.5, 10, 0]], {"1234": 0.65, "1324": 0.39, "1423": 0.35}),
+    "cap": ([[0, 0, 0], [1, 0, 0], [0.5, 0.866, 0], [0.5, 0.288, 0.093]],
+            {"1234": 0.010, "1243": 0.43, "1342": 0.43, "2341": 0.0096}),
+    "spade": ([[0, 0, 0], [1, -0.666, 0], [1, 0.666, 0], [1, 0, 0.443]],
+              {"1234": 0.084, "1243": 0.053, "1342": 0.060, "2134": 0.014, "2143": 0.14, "2341": 0.028}),
+    "regular": ([[0, 0, 0], [1, 0, 0], [0.5, 3 ** 0.5 / 2, 0], [0.5, 3 ** 0.5 / 6, (2 / 3) ** 0.5]], {"1234": 0.025}),
+}
+
+
+def mg_workload(args, g, torch):
+    """Multigrid solves on the default tet and Table 2 rates on the GPU."""
+    co = g.make_coeff(*COEFF[:3])
+    levels = []
+    for level, prec in [(5, g.MIXED), (6, g.MIXED), (7, g.MIXED), (8, g.MIXED), (9, g.F32)]:
+        t0 = time.time()
+        m = g.Multigrid(si.macro_tet(TET_SEED), level, coeff=co, poly_degree=DEG, nu=3, precision=prec)
+        setup_s = time.time() - t0
+        dt = torch.float32 if prec == g.F32 else torch.float64
+        rtol = 1e-5 if prec == g.F32 else 1e-8
+        b = torch.tensor(si.rhs(level, RHS_SEED), dtype=dt, device="cuda")
+        x = torch.zeros_like(b)
+        m.cycle(x, b, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        K = 5
+        e0.record()
+        m.cycle(x, b, K)
+        e1.record()
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / K
+        row = {"level": level, "precision": {g.MIXED: "MIXED", g.F32: "F32"}[prec], "interior_dof": interior(level),
+               "setup_s": round(setup_s, 3), "vcycle_ms": round(vms, 3), "rtol": rtol}
+        for name, meth in [("richardson", g.RICHARDSON), ("pcg", g.PCG)]:
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, rel, ok = m.solve(x, b, meth, rtol, 100)
+            torch.cuda.synchronize()
+            row[name] = {"iters": it, "rel": rel, "ok": ok, "ms": round((time.perf_counter() - t0) * 1e3, 3)}
+        levels.append(row)
+        m.close()
+    rates = []
+    for name, (V, cols) in TABLE2.items():
+        V = np.array(V, float)
+        for pi, paper in cols.items():
+            P = np.zeros_like(V)
+            for i, c in enumerate(pi):
+                P[int(c) - 1] = V[i]
+            m = g.Multigrid(P, 6, poly_degree=7, nu=3, precision=g.F64)
+            e = torch.tensor(si.interior_error(6, 9), dtype=torch.float64, device="cuda")
+            rho, _ = m.rate(e, 20)
+            m.close()
+            rates.append({"shape": name, "pi": pi, "rho_ilu_gpu": round(rho, 4), "rho_ilu_paper": paper})
+    l7 = [r for r in levels if r["level"] == LEVEL][0]
+    solve_ms = l7["richardson"]["ms"]
+    return {"metric": "multigrid solves to 1e-8: interior DoF solved per second (V-cycle iteration, L7 MIXED)",
+            "value": interior(LEVEL) / (solve_ms / 1e3), "unit": "DoF/s", "n_gpus": 1, "steps": 1, "warmup": 2,
+            "ms_per_step": solve_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", multigrid V(3,3) levels 2..7, solve to 1e-8 from x0 = 0",
+                       "precision": "MIXED", "parallelism": "replicas x1"},
+            "levels": levels, "table2_rates_deg7_f64": rates}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,7 +507,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg"])
     ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
@@ -453,7 +523,7 @@ def main():
     if args.workload != "single":
         if rank == 0:
             line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload,
-                    "smoothers": smoothers_workload}[args.workload](
+                    "smoothers": smoothers_workload, "mg": mg_workload}[args.workload](
                 args, g, torch)
             print(json.dumps(line), flush=True)
         return

@@ -55,6 +55,24 @@ def boundary_data(level: int, seed: int, scale: float = 1.0) -> np.ndarray:
     return uniform(seed, num_nodes(level), -scale, scale)
 
 
+def interior_error(level: int, seed: int) -> np.ndarray:
+    """A full-grid start error: U(-1, 1) on the interior points, 0 on the
+    boundary (lexicographic order, z slowest, then y, then x)."""
+    n = 2 ** level
+    v = uniform(seed, num_nodes(level), -1.0, 1.0)
+    k = 0
+    for z in range(n + 1):
+        for y in range(n + 1 - z):
+            m = n + 1 - z - y  # points of the row, x = 0 .. n - z - y
+            row = v[k:k + m]
+            row[0] = 0.0
+            row[m - 1] = 0.0
+            if y == 0 or z == 0:
+                row[:] = 0.0
+            k += m
+    return v
+
+
 def _aspect(P: np.ndarray) -> float:
     """Circumradius / (3 * inradius); 1 for a regular tetrahedron."""
     a, b, c, d = P

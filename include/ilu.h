@@ -80,7 +80,24 @@ typedef struct {
   long long max_wait_spins; /* bound on device-side spin waits; <=0: default */
   int kernel;          /* substitution kernels of FP32/MIXED sweeps: an ilu_kernel value */
   int factor;          /* factors the surrogates approximate: an ilu_factor value */
+  int stencil;         /* how a variable-kappa operator is applied: an ilu_stencil_mode value */
 } ilu_opts;
+
+/* How the residual applies A when kappa varies (constant kappa always uses
+ * its 15 constants).  The paper computes the residual by assembling A or by
+ * evaluating a surrogate of it (Sec. 4.1, residual step of Alg. 2):
+ *   ILU_STENCIL_ON_THE_FLY  assemble each row in the residual from kappa at
+ *                           the 15 neighbours (edge-star weights; about 230
+ *                           FP64 flops per point, no storage);
+ *   ILU_STENCIL_STORED      assemble the 14 off-diagonal coefficients of
+ *                           every interior row once at set-up, in FP64 on the
+ *                           device (14 x 8 bytes per grid point), and read
+ *                           them in the residual;
+ *   ILU_STENCIL_AUTO        stored when that array takes at most 4 GiB
+ *                           (level 9 and below), otherwise on the fly.
+ * Both give bit-identical residuals: the stored coefficients are the same
+ * FP64 sums, applied in the same order. */
+typedef enum { ILU_STENCIL_AUTO = 0, ILU_STENCIL_ON_THE_FLY = 1, ILU_STENCIL_STORED = 2 } ilu_stencil_mode;
 
 /* Which L D L^T preconditioner the surrogates approximate (Sec. 4.2):
  *   ILU_FACTOR_ILU0  exact ILU(0) of the interior block, by Alg. 1 (default);

@@ -662,8 +662,8 @@ __global__ void __launch_bounds__(256, 2) bwd_band(const DevTet *__restrict__ te
 
 // ------------------------------------------- residual / update (tiles) --
 
-// residual at one interior point, operator from t (constant stencil or
-// on-the-fly edge-star assembly); FP64 for double x
+// residual at one interior point, operator from t (OP 0 constant stencil,
+// 1 on-the-fly edge-star assembly, 2 stored coefficients); FP64 for double x
 // starts of the seven grid rows a point's stencil touches (one row (y, z))
 struct RowStarts {
   int64_t r0, rs, rn, rb, rbn, rt, rts;
@@ -674,7 +674,7 @@ __device__ __forceinline__ RowStarts row_starts(int N, int y, int z) {
           grid_index(N, 0, y - 1, z + 1)};
 }
 
-template <typename TX, typename TR, bool VAR>
+template <typename TX, typename TR, int OP>
 __device__ __forceinline__ TR residual_at(const DevTet &t, const RowStarts &R, int x, const TX *__restrict__ xv_,
                                           const TX *__restrict__ b) {
   const int64_t r0 = R.r0, rs = R.rs, rn = R.rn, rb = R.rb, rbn = R.rbn, rt = R.rt, rts = R.rts;
@@ -695,9 +695,11 @@ __device__ __forceinline__ TR residual_at(const DevTet &t, const RowStarts &R, i
   xv[13] = (TR)xv_[rt + x];
   xv[14] = (TR)xv_[rt + x - 1];
   TR res = (TR)b[r0 + x];
-  if (!VAR) {
+  if (OP == 0) {
 #pragma unroll
     for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
+  } else if (OP == 2) {
+    stored_apply(res, t.astore, t.astride, r0 + x, xv);
   } else {
     const double *kap = t.kappa;
     double kq[15];
@@ -749,7 +751,7 @@ __global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__
   const int s0 = 1 + 32 * c;
   const TX *xv = xs ? xs[lo] : x1;
   const TX *b = bs ? bs[lo] : b1;
-  const bool var = !t.const_kappa;
+  const int op = t.const_kappa ? 0 : (t.astore ? 2 : 1);
   double acc2 = 0.0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -759,7 +761,9 @@ __global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__
     if (y >= 1 && y <= N - 2 - z) {  // warp-uniform: the row's starts once per row
       const RowStarts R = row_starts(N, y, z);
       if (x >= 1 && x <= N - 1 - y - z) {
-        if (MODE == 0) r = var ? residual_at<TX, TR, true>(t, R, x, xv, b) : residual_at<TX, TR, false>(t, R, x, xv, b);
+        if (MODE == 0)
+          r = op == 0 ? residual_at<TX, TR, 0>(t, R, x, xv, b)
+                      : (op == 2 ? residual_at<TX, TR, 2>(t, R, x, xv, b) : residual_at<TX, TR, 1>(t, R, x, xv, b));
         else r = (TR)xv[R.r0 + x];
         acc2 += (double)r * (double)r;
       }

@@ -58,7 +58,8 @@ struct ilu_tet_s {
   DevTet *d_dev = nullptr;  // device copy of dev
   // FP32 band sweeps (band.cu): layout tables, band array, streams
   bool use_band = false;
-  int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO;
+  int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO, stencil_choice = ILU_STENCIL_AUTO;
+  double *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa)
   int band_Z = 8, band_ntiles = 0, band_ncta = 0;
   BandInfo *d_binfo = nullptr;
   int *d_bint = nullptr;  // CTA list, tile list, cluster map {0, ncta, 0}, tile prefix {0, ntiles}, epoch
@@ -99,7 +100,8 @@ void free_device(ilu_tet t) {
   for (auto e : t->ev_pool) cudaEventDestroy(e);
   t->ev_used.clear();
   t->ev_pool.clear();
-  cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa);
+  cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa); cudaFree(t->d_astore);
+  t->d_astore = nullptr;
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
   cudaFree(t->d_dev); cudaFree(t->d_map); cudaFree(t->d_chunks);
   t->d_dev = nullptr; t->d_map = nullptr; t->d_chunks = nullptr;
@@ -327,6 +329,19 @@ ilu_status upload(ilu_tet t) {
   d.tabF = t->d_tabF; d.tabB = t->d_tabB; d.kappa = t->d_kappa; d.w = t->d_w; d.flags = t->d_flags;
   std::memcpy(d.A15, h.A15, sizeof(d.A15));
   std::memcpy(d.Wstar, h.Wstar, sizeof(d.Wstar));
+  d.astore = nullptr;
+  d.astride = (int64_t)nn;
+  if (!h.const_kappa) {
+    const size_t abytes = (size_t)(kNumDirs - 1) * nn * sizeof(double);
+    const bool store = t->stencil_choice == ILU_STENCIL_STORED ||
+                       (t->stencil_choice == ILU_STENCIL_AUTO && abytes <= ((size_t)4 << 30));
+    if (store) {
+      CK(cudaMalloc(&t->d_astore, abytes), "cudaMalloc stored stencils");
+      CK(launch_stencil_store(d, t->d_astore, cudaStreamPerThread), "stencil assembly launch");
+      CK(cudaStreamSynchronize(cudaStreamPerThread), "stencil assembly");
+      d.astore = t->d_astore;
+    }
+  }
   return choose_clusters(t);
 }
 
@@ -595,6 +610,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->max_wait_spins = 0;
   o->kernel = ILU_KERNEL_AUTO;
   o->factor = ILU_FACTOR_ILU0;
+  o->stencil = ILU_STENCIL_AUTO;
   return ILU_OK;
 }
 
@@ -629,6 +645,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (o.precision < 0 || o.precision > 2) return fail(ILU_EINVAL, "unknown precision");
   if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_BAND) return fail(ILU_EINVAL, "unknown kernel choice");
   if (o.factor != ILU_FACTOR_ILU0 && o.factor != ILU_FACTOR_SGS) return fail(ILU_EINVAL, "unknown factor choice");
+  if (o.stencil < ILU_STENCIL_AUTO || o.stencil > ILU_STENCIL_STORED) return fail(ILU_EINVAL, "unknown stencil choice");
   int deg[3];
   for (int c = 0; c < 3; ++c) deg[c] = o.deg[c] >= 0 ? o.deg[c] : poly_degree;
   ilu_tet t = new (std::nothrow) ilu_tet_s;
@@ -664,6 +681,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
     choose_geometry(t, o.slabs);
     t->requested_slabs = o.slabs;
     t->kernel_choice = o.kernel;
+    t->stencil_choice = o.stencil;
     st = upload(t);
     if (st != ILU_OK) {
       free_device(t);

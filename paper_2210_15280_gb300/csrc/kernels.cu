@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <utility>
 
 #include "kernels.cuh"
@@ -32,11 +33,17 @@ namespace {
 // weights and kappa at the grid points
 struct StencilData {
   const double *A15, *Wstar, *kappa;
+  const double *astore;  // stored off-diagonal coefficients (MODE 2)
+  int64_t astride;
 };
+
+// MODE of the operator: 0 constant stencil, 1 assembled on the fly from
+// kappa, 2 stored coefficients (same values as 1)
+constexpr int kOpConst = 0, kOpStar = 1, kOpStored = 2;
 
 // r = b - A x at the interior points x0 + lane of row (y, z) (one warp, one
 // 32-point chunk of the row); returns this lane's share of ||r||^2
-template <typename TX, typename TR, typename TW, bool VAR>
+template <typename TX, typename TR, typename TW, int MODE>
 __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, int y, int z, int x0, int lane,
                                                  const TX *__restrict__ x, const TX *__restrict__ b,
                                                  TW *__restrict__ r) {
@@ -72,9 +79,11 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, in
     xv[13] = (TR)x[rt + xx];
     xv[14] = (TR)x[rt + xx - 1];
     TR res = (TR)b[r0 + xx];
-    if (!VAR) {
+    if (MODE == kOpConst) {
 #pragma unroll
       for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
+    } else if (MODE == kOpStored) {
+      stored_apply(res, t.astore, t.astride, r0 + xx, xv);
     } else {
       const double *kap = t.kappa;
       double kq[15];
@@ -103,17 +112,17 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, in
 
 // One tet: one warp per 32-point chunk of an interior row (the chunk list
 // balances rows of every length), 8 chunks per block, per-block partial norms.
-template <typename TX, typename TR, typename TW, bool VAR>
+template <typename TX, typename TR, typename TW, int MODE>
 __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__restrict__ x,
                                                        const TX *__restrict__ b, TW *__restrict__ r,
                                                        double *__restrict__ partials) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const StencilData sd{t.A15, t.Wstar, t.kappa};
+  const StencilData sd{t.A15, t.Wstar, t.kappa, t.astore, t.astride};
   const int ci = blockIdx.x * 8 + warp;
   double acc2 = 0.0;
   if (ci < t.nchunks) {
     const int ch = t.chunks[ci];
-    acc2 = residual_chunk<TX, TR, TW, VAR>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b, r);
+    acc2 = residual_chunk<TX, TR, TW, MODE>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b, r);
   }
   // deterministic block reduction of the squared norm
 #pragma unroll
@@ -155,12 +164,14 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
   if (ci >= tg.nchunks) return;  // no block-wide synchronisation follows
   const int ch = tg.chunks[ci];
   TW *r = reinterpret_cast<TW *>(tg.w);
-  const StencilData sd{sA, sW, tg.kappa};
+  const StencilData sd{sA, sW, tg.kappa, tg.astore, tg.astride};
   const int y = (ch >> 10) & 1023, z = ch >> 20, x0 = 1 + 32 * (ch & 1023);
   if (tg.const_kappa)
-    residual_chunk<TX, TR, TW, false>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
+    residual_chunk<TX, TR, TW, kOpConst>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
+  else if (tg.astore)
+    residual_chunk<TX, TR, TW, kOpStored>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
   else
-    residual_chunk<TX, TR, TW, true>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
+    residual_chunk<TX, TR, TW, kOpStar>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
 }
 
 // ------------------------------------------------- solver vector helpers --
@@ -282,29 +293,22 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
   if (nblocks_used) *nblocks_used = nb;
   if (nb == 0) return cudaSuccess;
   dim3 grid(nb);
-  const bool var = !t.const_kappa;
-  if (kind == kSweepF64) {
-    if (var)
-      residual_kernel<double, double, double, true><<<grid, 256, 0, st>>>(t, (const double *)x, (const double *)b,
-                                                                            (double *)r_out, partials);
-    else
-      residual_kernel<double, double, double, false><<<grid, 256, 0, st>>>(t, (const double *)x, (const double *)b,
-                                                                             (double *)r_out, partials);
-  } else if (kind == kSweepMixed) {
-    if (var)
-      residual_kernel<double, double, float, true><<<grid, 256, 0, st>>>(t, (const double *)x, (const double *)b,
-                                                                           (float *)r_out, partials);
-    else
-      residual_kernel<double, double, float, false><<<grid, 256, 0, st>>>(t, (const double *)x, (const double *)b,
-                                                                            (float *)r_out, partials);
-  } else {
-    if (var)
-      residual_kernel<float, float, float, true><<<grid, 256, 0, st>>>(t, (const float *)x, (const float *)b,
-                                                                         (float *)r_out, partials);
-    else
-      residual_kernel<float, float, float, false><<<grid, 256, 0, st>>>(t, (const float *)x, (const float *)b,
-                                                                          (float *)r_out, partials);
-  }
+  const int mode = t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar);
+  auto go = [&](auto tx, auto tr, auto tw, auto m) {
+    using TX = decltype(tx);
+    using TR = decltype(tr);
+    using TW = decltype(tw);
+    residual_kernel<TX, TR, TW, decltype(m)::value><<<grid, 256, 0, st>>>(t, (const TX *)x, (const TX *)b,
+                                                                          (TW *)r_out, partials);
+  };
+  auto by_mode = [&](auto tx, auto tr, auto tw) {
+    if (mode == kOpConst) go(tx, tr, tw, std::integral_constant<int, kOpConst>{});
+    else if (mode == kOpStored) go(tx, tr, tw, std::integral_constant<int, kOpStored>{});
+    else go(tx, tr, tw, std::integral_constant<int, kOpStar>{});
+  };
+  if (kind == kSweepF64) by_mode(double{}, double{}, double{});
+  else if (kind == kSweepMixed) by_mode(double{}, double{}, float{});
+  else by_mode(float{}, float{}, float{});
   return cudaGetLastError();
 }
 
@@ -320,6 +324,47 @@ cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n,
   else
     residual_batch_kernel<float, float, float><<<total_blocks, 256, 0, st>>>(
         tets, bprefix, n, reinterpret_cast<const float *const *>(xs), reinterpret_cast<const float *const *>(bs));
+  return cudaGetLastError();
+}
+
+namespace {
+// one warp per 32-point row chunk, as the residual
+__global__ void __launch_bounds__(256) stencil_store_kernel(DevTet t, double *__restrict__ A) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * 8 + warp;
+  if (ci >= t.nchunks) return;
+  const int ch = t.chunks[ci];
+  const int N = t.N, y = (ch >> 10) & 1023, z = ch >> 20, xx = 1 + 32 * (ch & 1023) + lane;
+  if (y + z > N - 2 || xx > N - 1 - y - z) return;
+  const int64_t r0 = grid_index(N, 0, y, z), rs = grid_index(N, 0, y - 1, z), rn = grid_index(N, 0, y + 1, z);
+  const int64_t rb = grid_index(N, 0, y, z - 1), rbn = grid_index(N, 0, y + 1, z - 1);
+  const int64_t rt = grid_index(N, 0, y, z + 1), rts = grid_index(N, 0, y - 1, z + 1);
+  const double *kap = t.kappa;
+  double kq[15];
+  kq[0] = kap[r0 + xx - 1];
+  kq[1] = kap[rs + xx];
+  kq[2] = kap[rs + xx + 1];
+  kq[3] = kap[rbn + xx - 1];
+  kq[4] = kap[rbn + xx];
+  kq[5] = kap[rb + xx];
+  kq[6] = kap[rb + xx + 1];
+  kq[7] = kap[r0 + xx];
+  kq[8] = kap[r0 + xx + 1];
+  kq[9] = kap[rn + xx];
+  kq[10] = kap[rn + xx - 1];
+  kq[11] = kap[rts + xx + 1];
+  kq[12] = kap[rts + xx];
+  kq[13] = kap[rt + xx];
+  kq[14] = kap[rt + xx - 1];
+  star_store_all(std::make_integer_sequence<int, 15>{}, kq, t.Wstar, A, t.astride, r0 + xx);
+}
+}  // namespace
+
+cudaError_t launch_stencil_store(const DevTet &t, double *A, cudaStream_t st) {
+  if (t.const_kappa || !t.kappa || !t.chunks) return cudaErrorInvalidValue;
+  const int nb = (t.nchunks + 7) / 8;
+  if (nb == 0) return cudaSuccess;
+  stencil_store_kernel<<<nb, 256, 0, st>>>(t, A);
   return cudaGetLastError();
 }
 

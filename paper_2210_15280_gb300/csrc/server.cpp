@@ -95,8 +95,9 @@ size_t num_nodes(int level) {
   return (N + 1) * (N + 2) * (N + 3) / 6;
 }
 
-// upper estimate of a tet's device memory: row tables, scratch, kappa,
-// Krylov vectors of ilu_solve, reduction buffers and launch bookkeeping
+// upper estimate of a tet's device memory: row tables, scratch, kappa and
+// its stored stencils, Krylov vectors of ilu_solve, reduction buffers and
+// launch bookkeeping
 size_t estimate_tet_bytes(int level, int precision, int degree, bool var) {
   const size_t N = (size_t)1 << level, nn = num_nodes(level);
   const size_t ew = precision == ILU_F64 ? 8 : 4, ex = precision == ILU_F32 ? 4 : 8;
@@ -105,6 +106,7 @@ size_t estimate_tet_bytes(int level, int precision, int degree, bool var) {
   size_t b = rows * 15 * rstride * ew;  // forward + backward row tables
   b += nn * ew;                         // scratch w
   if (var) b += nn * 8;                 // kappa
+  if (var && 14 * nn * 8 <= ((size_t)4 << 30)) b += 14 * nn * 8;  // stored stencils (ILU_STENCIL_AUTO)
   b += 5 * nn * ex;                     // Krylov vectors
   b += (N * N / 8 + 4096) * 8;          // partial sums, flags, norms
   return b + (1u << 20);                // allocation granularity

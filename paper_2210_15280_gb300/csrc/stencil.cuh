@@ -36,6 +36,35 @@ __device__ __forceinline__ void star_apply(TR &res, const double *kq, const TR *
   }
 }
 
+// A_d of one direction alone
+template <int D>
+__device__ __forceinline__ double star_coeff(const double *kq, const double *W) {
+  constexpr int b = star_begin(D), e = star_begin(D + 1);
+  return star_sum<b>(std::make_integer_sequence<int, e - b>{}, kq, W);
+}
+
+// plane of direction d in the stored operator (the centre has none)
+ILU_HDC int store_plane(int d) { return d < kCentre ? d : d - 1; }
+
+template <int... D>
+__device__ __forceinline__ void star_store_all(std::integer_sequence<int, D...>, const double *kq, const double *W,
+                                               double *A, int64_t stride, int64_t i) {
+  ((D != kCentre ? (void)(A[store_plane(D) * stride + i] = star_coeff<D>(kq, W)) : (void)0), ...);
+}
+
+// the same application as star_apply_all with coefficients read from the
+// stored planes: identical operands, identical order, identical result
+template <typename TR>
+__device__ __forceinline__ void stored_apply(TR &res, const double *__restrict__ A, int64_t stride, int64_t i,
+                                             const TR *xv) {
+  const double xc = (double)xv[kCentre];
+#pragma unroll
+  for (int d = 0; d < kNumDirs; ++d) {
+    if (d == kCentre) continue;
+    res = (TR)fma(-A[store_plane(d) * stride + i], (double)xv[d] - xc, (double)res);
+  }
+}
+
 template <typename TR, int... D>
 __device__ __forceinline__ void star_apply_all(std::integer_sequence<int, D...>, TR &res, const double *kq,
                                                const TR *xv, const double *W) {

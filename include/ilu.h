@@ -81,7 +81,17 @@ typedef struct {
   int kernel;          /* substitution kernels of FP32/MIXED sweeps: an ilu_kernel value */
   int factor;          /* factors the surrogates approximate: an ilu_factor value */
   int stencil;         /* how a variable-kappa operator is applied: an ilu_stencil_mode value */
+  int orient;          /* vertex order used: an ilu_orient value */
 } ilu_opts;
+
+/* Which vertex order of the macro-tetrahedron the handle uses (Sec. 3):
+ *   ILU_ORIENT_GIVEN  p1..p4 as passed (default);
+ *   ILU_ORIENT_LFA    the order ilu_lfa_order picks.  The logical grid, and
+ *                     with it the layout of every vector, is then that of the
+ *                     reordered tet: ilu_vertex_order tells which.
+ * The ILU(0) smoother depends on the order (the lexicographic order of the
+ * points follows the vertices); symmetric Gauss-Seidel does too. */
+typedef enum { ILU_ORIENT_GIVEN = 0, ILU_ORIENT_LFA = 1 } ilu_orient;
 
 /* How the residual applies A when kappa varies (constant kappa always uses
  * its 15 constants).  The paper computes the residual by assembling A or by
@@ -174,6 +184,25 @@ ilu_status ilu_exact_factor(ilu_tet t, int x, int y, int z, double out[8]);
 /* Host FP64 stencil A^p_d of the full operator at grid point (x,y,z) (all 15
  * directions in the order w s se bnw bn bc be c e n nw tse ts tc tw). */
 ilu_status ilu_stencil(ilu_tet t, int x, int y, int z, double out[15]);
+
+/* Local Fourier analysis of the ILU(0) smoother for the 24 vertex orders of
+ * a macro-tetrahedron (Sec. 3): for each order, the constant stencil with
+ * kappa = 1, its asymptotic ILU stencil (the stencil equations of Sec. 3,
+ * Gauss-Seidel iteration from L_c = D_c = 1, L_d = 0), and the smoothing
+ * factor mu = max |1 - A(t) / (L(t) D conj(L(t)))| over the high frequencies
+ * of a 16^3 grid of (-pi, pi)^3 (t_k = -pi + 2 pi k / 16; at least one
+ * component with |t| >= pi/2).
+ *   perm    (host, out) perm[i] = index 0..3 of the vertex placed at
+ *           position i by the order with the smallest mu (the first in
+ *           lexicographic order among factors equal to 1e-12 relative).
+ *   mu      (host, nullable) its factor.
+ *   mu_all  (host, nullable, 24) the factors of all orders, lexicographic.
+ * Host only.  ILU_EINVAL for a degenerate tet. */
+ilu_status ilu_lfa_order(const double macro_tet[12], int perm[4], double *mu, double mu_all[24]);
+
+/* The vertex order a handle uses: perm[i] = index of the caller's vertex at
+ * position i (the identity unless set up with ILU_ORIENT_LFA). */
+ilu_status ilu_vertex_order(ilu_tet t, int perm[4]);
 
 /* ------------------------------------------------------------- smoothing -- */
 

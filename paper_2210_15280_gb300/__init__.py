@@ -23,6 +23,7 @@ RICHARDSON, PCG = 0, 1
 KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND = 0, 1, 2
 FACTOR_ILU0, FACTOR_SGS = 0, 1
 STENCIL_AUTO, STENCIL_ON_THE_FLY, STENCIL_STORED = 0, 1, 2
+ORIENT_GIVEN, ORIENT_LFA = 0, 1
 STATUS_NAMES = ["ILU_OK", "ILU_EINVAL", "ILU_ENOMEM", "ILU_ECUDA", "ILU_ESINGULAR", "ILU_ENOTCONV",
                 "ILU_ETIMEOUT", "ILU_EBUSY", "ILU_ENODEV"]
 
@@ -35,6 +36,7 @@ EXPORTS = [
     "ilu_server_stats", "ilu_server_destroy", "ilu_num_nodes", "ilu_num_interior", "ilu_index",
     "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read", "ilu_residual_noalloc",
     "ilu_mg_setup", "ilu_mg_destroy", "ilu_mg_level", "ilu_mg_cycle", "ilu_mg_solve", "ilu_mg_rate",
+    "ilu_lfa_order", "ilu_vertex_order",
 ]
 
 
@@ -52,7 +54,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("deg", ctypes.c_int * 3), ("sample_level", ctypes.c_int), ("ridge", ctypes.c_double),
                 ("precision", ctypes.c_int), ("slabs", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_wait_spins", ctypes.c_longlong), ("kernel", ctypes.c_int), ("factor", ctypes.c_int),
-                ("stencil", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("orient", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -120,6 +122,8 @@ def lib():
         L.ilu_mg_cycle.argtypes = [vp, vp, vp, i, vp, vp]
         L.ilu_mg_solve.argtypes = [vp, vp, vp, i, d, i, vp, vp, vp]
         L.ilu_mg_rate.argtypes = [vp, vp, i, vp, vp, vp]
+        L.ilu_lfa_order.argtypes = [P(ctypes.c_double * 12), vp, vp, vp]
+        L.ilu_vertex_order.argtypes = [vp, vp]
         L.ilu_profile_enable.argtypes = [vp, i]
         L.ilu_profile_read.argtypes = [vp, vp, P(ctypes.c_longlong)]
         L.ilu_num_nodes.argtypes = [i]; L.ilu_num_nodes.restype = sz
@@ -180,7 +184,7 @@ def _stream(stream):
 
 
 def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, device=0, max_wait_spins=0,
-              kernel=0, factor=0, stencil=0):
+              kernel=0, factor=0, stencil=0, orient=0):
     o = Opts()
     lib().ilu_opts_default(ctypes.byref(o))
     if deg is not None:
@@ -192,12 +196,25 @@ def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, d
     o.kernel = int(kernel)
     o.factor = int(factor)
     o.stencil = int(stencil)
+    o.orient = int(orient)
     return o
 
 
 def make_coeff(kind="const", c0=1.0, amp=0.0, ipow=0):
     k = {"const": COEFF_CONST, "sinprod": COEFF_SINPROD, "kappa_i": COEFF_KAPPA_I}.get(kind, kind)
     return Coeff(int(k), float(c0), float(amp), int(ipow))
+
+
+def lfa_order(macro_tet):
+    """(perm, mu, mu_all): the vertex order with the smallest LFA smoothing
+    factor of the ILU(0) smoother (perm[i] = index of the vertex placed at
+    position i), its factor and the factors of all 24 orders."""
+    P = (ctypes.c_double * 12)(*np.asarray(macro_tet, dtype=np.float64).reshape(12))
+    perm = np.zeros(4, dtype=np.int32)
+    mu = np.zeros(1)
+    mus = np.zeros(24)
+    _check(lib().ilu_lfa_order(ctypes.byref(P), _ptr(perm), _ptr(mu), _ptr(mus)))
+    return [int(v) for v in perm], float(mu[0]), mus
 
 
 class Tet:
@@ -290,6 +307,11 @@ class Tet:
         n = ctypes.c_longlong(0)
         _check(lib().ilu_profile_read(self.h, _ptr(ms), ctypes.byref(n)))
         return ms, n.value
+
+    def vertex_order(self):
+        perm = np.zeros(4, dtype=np.int32)
+        _check(lib().ilu_vertex_order(self.h, _ptr(perm)))
+        return [int(v) for v in perm]
 
     def stencil(self, x, y, z):
         out = np.zeros(15)

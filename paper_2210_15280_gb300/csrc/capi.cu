@@ -59,6 +59,7 @@ struct ilu_tet_s {
   // FP32 band sweeps (band.cu): layout tables, band array, streams
   bool use_band = false;
   int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO, stencil_choice = ILU_STENCIL_AUTO;
+  int perm[4] = {0, 1, 2, 3};  // vertex order used (ILU_ORIENT_LFA)
   double *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa)
   int band_Z = 8, band_ntiles = 0, band_ncta = 0;
   BandInfo *d_binfo = nullptr;
@@ -611,6 +612,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->kernel = ILU_KERNEL_AUTO;
   o->factor = ILU_FACTOR_ILU0;
   o->stencil = ILU_STENCIL_AUTO;
+  o->orient = ILU_ORIENT_GIVEN;
   return ILU_OK;
 }
 
@@ -646,18 +648,28 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_BAND) return fail(ILU_EINVAL, "unknown kernel choice");
   if (o.factor != ILU_FACTOR_ILU0 && o.factor != ILU_FACTOR_SGS) return fail(ILU_EINVAL, "unknown factor choice");
   if (o.stencil < ILU_STENCIL_AUTO || o.stencil > ILU_STENCIL_STORED) return fail(ILU_EINVAL, "unknown stencil choice");
+  if (o.orient != ILU_ORIENT_GIVEN && o.orient != ILU_ORIENT_LFA) return fail(ILU_EINVAL, "unknown orientation choice");
+  int perm[4] = {0, 1, 2, 3};
+  if (o.orient == ILU_ORIENT_LFA) {
+    ilu_status ls = ilu_lfa_order(macro_tet, perm, nullptr, nullptr);
+    if (ls != ILU_OK) return ls;
+  }
+  double Pv[12];
+  for (int i = 0; i < 4; ++i)
+    for (int c = 0; c < 3; ++c) Pv[3 * i + c] = macro_tet[3 * perm[i] + c];
   int deg[3];
   for (int c = 0; c < 3; ++c) deg[c] = o.deg[c] >= 0 ? o.deg[c] : poly_degree;
   ilu_tet t = new (std::nothrow) ilu_tet_s;
   if (!t) return fail(ILU_ENOMEM, "out of host memory");
   t->precision = o.precision;
   t->device = o.device;
+  std::memcpy(t->perm, perm, sizeof(perm));
   t->max_spins = o.max_wait_spins > 0 ? o.max_wait_spins : kDefaultSpins;
   std::string err;
   ilu_status st;
   try {
     t->host.factor = o.factor;
-    st = host_setup(t->host, macro_tet, level, coeff, deg, o.sample_level, o.ridge, err);
+    st = host_setup(t->host, Pv, level, coeff, deg, o.sample_level, o.ridge, err);
   } catch (const std::bad_alloc &) {
     st = ILU_ENOMEM;
     err = "out of host memory during set-up";
@@ -697,6 +709,12 @@ ilu_status ilu_destroy(ilu_tet t) {
   if (!t) return ILU_OK;
   free_device(t);
   delete t;
+  return ILU_OK;
+}
+
+ilu_status ilu_vertex_order(ilu_tet t, int perm[4]) {
+  if (!t || !perm) return fail(ILU_EINVAL, "null argument");
+  std::memcpy(perm, t->perm, sizeof(t->perm));
   return ILU_OK;
 }
 

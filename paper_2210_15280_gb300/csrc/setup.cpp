@@ -184,6 +184,31 @@ static bool stencil_weights(HostTet &t, std::string &err) {
   return true;
 }
 
+bool unit_stencil(const double P[12], double A[15], std::string &err) {
+  double e[3][3], scale = 0.0;
+  for (int k = 0; k < 12; ++k)
+    if (!std::isfinite(P[k])) { err = "macro-tetrahedron has non-finite coordinates"; return false; }
+  for (int m = 0; m < 3; ++m)
+    for (int c = 0; c < 3; ++c) {
+      e[m][c] = P[3 * (m + 1) + c] - P[c];
+      scale = std::max(scale, std::fabs(e[m][c]));
+    }
+  const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+  if (!(std::fabs(det) > 1e-12 * scale * scale * scale)) { err = "degenerate macro-tetrahedron"; return false; }
+  HostTet t;
+  t.L = 2;
+  t.N = 4;
+  t.h = 0.25;
+  std::memcpy(t.P, P, sizeof(double) * 12);
+  t.coeff = ilu_coeff{ILU_COEFF_CONST, 1.0, 0.0, 0};
+  t.const_kappa = true;
+  element_classes(t);
+  if (!stencil_weights(t, err)) return false;
+  std::memcpy(A, t.A15, sizeof(double) * 15);
+  return true;
+}
+
 void host_stencil(const HostTet &t, int x, int y, int z, double A[15]) {
   if (t.const_kappa) {
     for (int d = 0; d < 15; ++d) A[d] = t.A15[d];

@@ -42,6 +42,9 @@ ilu_status host_setup(HostTet &t, const double P[12], int level, const ilu_coeff
                       int sample_level, double ridge, std::string &err);
 // (Re)build the row tables from t.coefs.
 void build_row_tables(HostTet &t);
+// Constant 15-point stencil of a tet with kappa = 1 at level 2 (the values at
+// level L are these times 2^(2-L)).  False (with err) for a degenerate tet.
+bool unit_stencil(const double P[12], double A[15], std::string &err);
 // Stencil of the full operator at a grid point (15 directions).
 void host_stencil(const HostTet &t, int x, int y, int z, double A[15]);
 // Evaluate the eight surrogates from the FP64 row tables (V2-masked L).

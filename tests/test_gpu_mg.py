@@ -143,3 +143,19 @@ def test_rate_matches_oracle_exact_rates(g, orc, omg):
         rg, hist = m.rate(dev(full, torch.float64))
         m.close()
         assert lo <= ro <= hi and lo <= rg <= hi, (ro, rg)
+
+
+def test_lfa_orientation_in_multigrid(g, orc):
+    """The Spindle as given converges at rho ~ 0.65; set up with
+    ILU_ORIENT_LFA the hierarchy uses the order the smoothing factor picks
+    and converges at ~ 0.39 (Table 2)."""
+    P = np.array([[0, 0, 0.5], [0, 0, -0.5], [0.5, 10, 0], [-0.5, 10, 0]])
+    e = si.interior_error(6, 9)
+    out = {}
+    for orient in [g.ORIENT_GIVEN, g.ORIENT_LFA]:
+        m = g.Multigrid(P, 6, poly_degree=7, nu=3, precision=g.F64, orient=orient)
+        out[orient], _ = m.rate(dev(e, torch.float64))
+        if orient == g.ORIENT_LFA:
+            assert m.tet(6).vertex_order() == g.lfa_order(P)[0]
+        m.close()
+    assert 0.6 < out[g.ORIENT_GIVEN] < 0.7 and 0.36 < out[g.ORIENT_LFA] < 0.42, out

@@ -23,8 +23,9 @@ Further workloads print a line of the same form (not the default run):
   --workload serve   the request loop: Poisson arrivals (mean gap 0.5 ms) of
                      interior solves on macro-tets of that mesh, levels 5-6
                      (Richardson) or 5-8 (--method pcg), mixed coefficients,
-                     to 1e-8; solves/s and p50/p99 latency, beside the same
-                     requests solved one after another with FP64 sweeps.
+                     to 1e-8 (--method mg: levels 5-8, V(3,3) multigrid);
+                     solves/s and p50/p99 latency, beside the same requests
+                     solved one after another with FP64 sweeps.
   --workload smoothers  iteration counts of the surrogate ILU(0) smoother
                      against the surrogate symmetric Gauss-Seidel smoother,
                      both as Richardson smoothers and as CG preconditioners,
@@ -314,14 +315,15 @@ def serve_workload(args, g, torch):
     """Poisson stream of interior solves through the request loop, against the
     same requests solved one after another with FP64 sweeps."""
     pcg = args.method == "pcg"
+    mg = args.method == "mg"
     nreq = args.requests
     pool = si.macro_mesh(6, n_tets=32)
-    lo, hi = (5, 8) if pcg else (5, 6)
+    lo, hi = (5, 8) if (pcg or mg) else (5, 6)
     levels = si.batch_levels(11, nreq, lo, hi)
     kinds = [("const", 1.0, 0.0, 0), ("sinprod", 1.0, 0.5, 0), ("kappa_i", 0.0, 0.0, 2)]
     which = si.splitmix64(12, nreq) % len(pool)
     arrivals = si.poisson_arrivals(13, nreq, 0.5e-3)  # seconds from the first submit
-    method = g.PCG if pcg else g.RICHARDSON
+    method = g.PCG if pcg else (g.MG_VCYCLE if mg else g.RICHARDSON)
     reqs = []
     for i in range(nreq):
         L = int(levels[i])
@@ -355,14 +357,15 @@ def serve_workload(args, g, torch):
     for r in reqs:
         key = (id(r["P"]), r["level"], r["co"])
         if key not in seq:
-            seq[key] = g.Tet(r["P"], r["level"], coeff=g.make_coeff(*r["co"]), poly_degree=5, precision=g.F64)
+            make = g.Multigrid if mg else g.Tet
+            seq[key] = make(r["P"], r["level"], coeff=g.make_coeff(*r["co"]), poly_degree=5, precision=g.F64)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for r in reqs:
         t = seq[(id(r["P"]), r["level"], r["co"])]
         x = torch.zeros(si.num_nodes(r["level"]), dtype=torch.float64, device="cuda")
         b = torch.tensor(r["b"], dtype=torch.float64, device="cuda")
-        t.solve(x, b, method, 1e-8, 100000)
+        t.solve(x, b, g.RICHARDSON if mg else method, 1e-8, 100000)
         x.cpu()
     seq_rate = nreq / (time.perf_counter() - t1)
     q = lambda p: float(lat[min(len(lat) - 1, max(0, int(np.ceil(p * len(lat))) - 1))])
@@ -371,7 +374,8 @@ def serve_workload(args, g, torch):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": f"{nreq} Poisson-arrival requests (mean gap 0.5 ms), levels {lo}-{hi}, "
-                                   f"{'PCG' if pcg else 'Richardson'} to 1e-8, MIXED, 32 macro-tets x 3 kappa",
+                                   f"{'PCG' if pcg else ('V(3,3) multigrid' if mg else 'Richardson')} to 1e-8, "
+                                   "MIXED, 32 macro-tets x 3 kappa",
                        "parallelism": "replicas x1"},
             "p50_ms": q(0.5), "p99_ms": q(0.99), "completed": ok, "max_concurrent": st["max_concurrent"],
             "sequential_f64_solves_per_s": seq_rate,
@@ -508,7 +512,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg"])
-    ap.add_argument("--method", default="richardson", choices=["richardson", "pcg"])
+    ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
     ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

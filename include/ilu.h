@@ -238,7 +238,11 @@ ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double
  * before any stream capture.  Asynchronous on `stream`; calls no allocator. */
 ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void *b, void *r, double *norm_dev, void *stream);
 
-typedef enum { ILU_RICHARDSON = 0, ILU_PCG = 1 } ilu_method;
+/* Outer iterations.  ilu_solve takes ILU_RICHARDSON or ILU_PCG; ilu_mg_solve
+ * takes those two (V-cycle iteration, V-cycle-preconditioned CG) or their
+ * multigrid names; a request of the request loop takes all four, the last two
+ * selecting a resident multigrid hierarchy instead of a single tet. */
+typedef enum { ILU_RICHARDSON = 0, ILU_PCG = 1, ILU_MG_VCYCLE = 2, ILU_MG_PCG = 3 } ilu_method;
 
 /* Solve A x = b on the interior (boundary of x = Dirichlet data) to
  * ||b - A x||_2 <= rtol ||b||_2 (interior norms) with smoothed Richardson
@@ -343,7 +347,7 @@ typedef struct {
   int level;
   ilu_coeff coeff;
   int poly_degree;
-  int method;        /* ilu_method */
+  int method;        /* ilu_method; ILU_MG_VCYCLE / ILU_MG_PCG: V(3,3) multigrid, level >= 3 */
   double rtol;
   int max_iter;
   const double *b;   /* host, full grid, ilu_num_nodes(level) doubles; copied on submit */

@@ -19,7 +19,7 @@ _lib = None
 ILU_OK, ILU_EINVAL, ILU_ENOMEM, ILU_ECUDA, ILU_ESINGULAR, ILU_ENOTCONV, ILU_ETIMEOUT, ILU_EBUSY, ILU_ENODEV = range(9)
 F64, F32, MIXED = 0, 1, 2
 COEFF_CONST, COEFF_SINPROD, COEFF_KAPPA_I = 0, 1, 2
-RICHARDSON, PCG = 0, 1
+RICHARDSON, PCG, MG_VCYCLE, MG_PCG = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND = 0, 1, 2
 FACTOR_ILU0, FACTOR_SGS = 0, 1
 STENCIL_AUTO, STENCIL_ON_THE_FLY, STENCIL_STORED = 0, 1, 2

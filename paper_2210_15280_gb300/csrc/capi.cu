@@ -856,6 +856,7 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
   ilu_status st = check_usable(t);
   if (st != ILU_OK) return st;
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
+  if (method == ILU_MG_VCYCLE || method == ILU_MG_PCG) return fail(ILU_EINVAL, "multigrid methods need ilu_mg_solve");
   if (method != ILU_RICHARDSON && method != ILU_PCG) return fail(ILU_EINVAL, "unknown method");
   if (!(rtol >= 0.0) || max_iter < 0) return fail(ILU_EINVAL, "bad tolerance or iteration limit");
   std::lock_guard<std::mutex> lk(t->mu);

@@ -331,6 +331,8 @@ ilu_status ilu_mg_solve(ilu_mg m, void *x, const void *b, int method, double rto
                         int *iters, double *rel_res) {
   MS(check_mg(m));
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
+  if (method == ILU_MG_VCYCLE) method = ILU_RICHARDSON;
+  if (method == ILU_MG_PCG) method = ILU_PCG;
   if (method != ILU_RICHARDSON && method != ILU_PCG) return fail(ILU_EINVAL, "unknown method");
   if (!(rtol >= 0.0) || max_iter < 0) return fail(ILU_EINVAL, "bad tolerance or iteration limit");
   cudaStream_t st = (cudaStream_t)stream;

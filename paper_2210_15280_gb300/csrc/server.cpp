@@ -18,6 +18,10 @@
 // requests on other tets go ahead.  A request that cannot fit even in an
 // empty device fails with ILU_ENOMEM.
 //
+// Multigrid requests (ILU_MG_VCYCLE, ILU_MG_PCG) are served by a resident
+// multigrid hierarchy (ilu_mg) instead of a single tet handle, keyed
+// separately; their solves take a handful of V-cycles at any level.
+//
 // Every request runs the same kernels on its own vectors whatever else is
 // admitted, so its result does not depend on the mix.
 #include <cuda_runtime.h>
@@ -55,7 +59,7 @@ ilu_status fail(ilu_status s, const std::string &msg) {
 // identity of a set-up tet
 struct Key {
   double P[12];
-  int level, kind, ipow, degree;
+  int level, kind, ipow, degree, mg;
   double c0, amp;
   bool operator<(const Key &o) const {
     int c = std::memcmp(P, o.P, sizeof(P));
@@ -64,14 +68,28 @@ struct Key {
     if (kind != o.kind) return kind < o.kind;
     if (ipow != o.ipow) return ipow < o.ipow;
     if (degree != o.degree) return degree < o.degree;
+    if (mg != o.mg) return mg < o.mg;
     c = std::memcmp(&c0, &o.c0, sizeof(double));
     if (c) return c < 0;
     return std::memcmp(&amp, &o.amp, sizeof(double)) < 0;
   }
 };
 
-struct Resident {
+// a resident set-up: one tet handle, or a multigrid hierarchy
+struct Handle {
   ilu_tet t = nullptr;
+  ilu_mg m = nullptr;
+  explicit operator bool() const { return t || m; }
+  void destroy() {
+    if (t) ilu_destroy(t);
+    if (m) ilu_mg_destroy(m);
+    t = nullptr;
+    m = nullptr;
+  }
+};
+
+struct Resident {
+  Handle t;
   size_t bytes = 0;
   bool busy = false;
   std::list<Key>::iterator lru;  // position in the idle list (valid when !busy)
@@ -134,7 +152,7 @@ struct ilu_server_s {
 
   // pick the first queued job that can run now; evicts idle tets to make
   // room; fails jobs that can never fit.  Called with mu held.
-  bool pick(uint64_t *out, std::vector<ilu_tet> *evict) {
+  bool pick(uint64_t *out, std::vector<Handle> *evict) {
     for (auto it = queue.begin(); it != queue.end(); ++it) {
       Job &j = jobs[*it];
       auto r = resident.find(j.key);
@@ -196,12 +214,12 @@ struct ilu_server_s {
   }
 
   void slot_main();
-  ilu_status run(Job &j, ilu_tet t, cudaStream_t st, int *iters, double *rel);
+  ilu_status run(Job &j, Handle t, cudaStream_t st, int *iters, double *rel);
 };
 
 // one request on its tet: vectors in, ilu_solve, solution out; the vectors
 // are stream-ordered allocations returned when the request ends
-ilu_status ilu_server_s::run(Job &j, ilu_tet t, cudaStream_t st, int *iters, double *rel) {
+ilu_status ilu_server_s::run(Job &j, Handle t, cudaStream_t st, int *iters, double *rel) {
   const size_t nn = num_nodes(j.req.level);
   const bool f32 = opts.precision == ILU_F32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
@@ -229,7 +247,9 @@ ilu_status ilu_server_s::run(Job &j, ilu_tet t, cudaStream_t st, int *iters, dou
     return cudaStreamSynchronize(st) == cudaSuccess;  // tmp is reused
   };
   if (!put(*db, j.b) || !put(*dx, j.x0)) return fail(ILU_ECUDA, "upload of b or x0");
-  ilu_status s = ilu_solve(t, *dx, *db, j.req.method, j.req.rtol, j.req.max_iter, st, iters, rel);
+  ilu_status s = t.m ? ilu_mg_solve(t.m, *dx, *db, j.req.method == ILU_MG_PCG ? ILU_PCG : ILU_RICHARDSON, j.req.rtol,
+                                    j.req.max_iter, st, iters, rel)
+                     : ilu_solve(t.t, *dx, *db, j.req.method, j.req.rtol, j.req.max_iter, st, iters, rel);
   if (s != ILU_OK && s != ILU_ENOTCONV) return s;
   j.x.resize(nn);
   if (!f32) {
@@ -252,8 +272,8 @@ void ilu_server_s::slot_main() {
                   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
   for (;;) {
     uint64_t tk = 0;
-    std::vector<ilu_tet> evict;
-    ilu_tet t = nullptr;
+    std::vector<Handle> evict;
+    Handle t;
     {
       std::unique_lock<std::mutex> lk(mu);
       for (;;) {
@@ -261,7 +281,7 @@ void ilu_server_s::slot_main() {
         if (pick(&tk, &evict)) break;
         if (!evict.empty()) {  // free what was evicted before sleeping
           lk.unlock();
-          for (ilu_tet e : evict) ilu_destroy(e);
+          for (Handle &e : evict) e.destroy();
           evict.clear();
           lk.lock();
           continue;
@@ -282,7 +302,7 @@ void ilu_server_s::slot_main() {
       ++active;
       max_active = std::max(max_active, active);
     }
-    for (ilu_tet e : evict) ilu_destroy(e);
+    for (Handle &e : evict) e.destroy();
     Job &j = jobs[tk];  // stable: unordered_map references survive rehashing
     ilu_status s = ILU_OK;
     int iters = 0;
@@ -294,7 +314,10 @@ void ilu_server_s::slot_main() {
       ilu_opts_default(&o);
       o.precision = opts.precision;
       o.device = opts.device;
-      s = ilu_setup(j.req.macro_tet, j.req.level, &j.req.coeff, j.req.poly_degree, &o, &t);
+      if (j.key.mg)
+        s = ilu_mg_setup(j.req.macro_tet, j.req.level, &j.req.coeff, j.req.poly_degree, 3, &o, &t.m);
+      else
+        s = ilu_setup(j.req.macro_tet, j.req.level, &j.req.coeff, j.req.poly_degree, &o, &t.t);
       fresh = true;
     }
     if (s == ILU_OK) s = run(j, t, st, &iters, &rel);
@@ -328,7 +351,7 @@ void ilu_server_s::slot_main() {
       else evict.clear();
       finish(tk, s, iters, rel);
     }
-    for (ilu_tet e : evict) ilu_destroy(e);
+    for (Handle &e : evict) e.destroy();
     cv_work.notify_all();
   }
   if (st) {
@@ -379,7 +402,9 @@ ilu_status ilu_server_submit(ilu_server s, const ilu_request *req, uint64_t *tic
   if (!s || !req || !ticket) return fail(ILU_EINVAL, "null argument");
   if (req->level < 2 || req->level > kMaxLevel) return fail(ILU_EINVAL, "level out of [2, 10]");
   if (!req->b) return fail(ILU_EINVAL, "null right-hand side");
-  if (req->method != ILU_RICHARDSON && req->method != ILU_PCG) return fail(ILU_EINVAL, "unknown method");
+  if (req->method < ILU_RICHARDSON || req->method > ILU_MG_PCG) return fail(ILU_EINVAL, "unknown method");
+  const bool mg = req->method == ILU_MG_VCYCLE || req->method == ILU_MG_PCG;
+  if (mg && req->level < 3) return fail(ILU_EINVAL, "multigrid needs level >= 3");
   if (!(req->rtol >= 0.0) || req->max_iter < 0) return fail(ILU_EINVAL, "bad tolerance or iteration limit");
   if (req->poly_degree < 0 || req->poly_degree > 12) return fail(ILU_EINVAL, "degree out of [0, 12]");
   const size_t nn = num_nodes(req->level);
@@ -401,9 +426,18 @@ ilu_status ilu_server_submit(ilu_server s, const ilu_request *req, uint64_t *tic
   j.key.c0 = req->coeff.c0;
   j.key.amp = req->coeff.amp;
   j.key.degree = req->poly_degree;
+  j.key.mg = mg ? 1 : 0;
   const size_t ex = s->opts.precision == ILU_F32 ? 4 : 8;
   j.vec_bytes = 2 * nn * ex;
-  j.tet_bytes = estimate_tet_bytes(req->level, s->opts.precision, req->poly_degree, req->coeff.kind != ILU_COEFF_CONST);
+  const bool var = req->coeff.kind != ILU_COEFF_CONST;
+  if (mg) {  // a tet per level 3..L, and per level x, b, r plus five Krylov vectors at the finest
+    j.tet_bytes = 0;
+    for (int l = 3; l <= req->level; ++l)
+      j.tet_bytes += estimate_tet_bytes(l, s->opts.precision, req->poly_degree, var) + 3 * num_nodes(l) * ex;
+    j.tet_bytes += 5 * nn * ex;
+  } else {
+    j.tet_bytes = estimate_tet_bytes(req->level, s->opts.precision, req->poly_degree, var);
+  }
   j.t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -482,7 +516,7 @@ ilu_status ilu_server_destroy(ilu_server s) {
   }
   s->cv_work.notify_all();
   for (auto &th : s->slots) th.join();
-  for (auto &kv : s->resident) ilu_destroy(kv.second.t);
+  for (auto &kv : s->resident) kv.second.t.destroy();
   delete s;
   return ILU_OK;
 }

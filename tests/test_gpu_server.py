@@ -107,3 +107,41 @@ def test_wait_with_time_limit_and_repeat_request(g):
     assert np.array_equal(first["x"], second["x"])
     assert second["latency_ms"] < first["latency_ms"]
     s.close()
+
+
+def test_multigrid_requests(g, orc):
+    """ILU_MG_VCYCLE / ILU_MG_PCG requests are served by resident multigrid
+    hierarchies: a few cycles at any level, the same result alone and in a
+    mix with single-level requests, and the assembled system's solution."""
+    mesh = si.macro_mesh(9, n_tets=6)
+    reqs = []
+    for i in range(6):
+        L = 4 + i % 3
+        reqs.append(dict(P=mesh[i], level=L, co=COEFFS[i % 3], deg=5, b=si.rhs(L, 900 + i),
+                         x0=si.boundary_data(L, 950 + i) * 0.1, method=[g.MG_VCYCLE, g.MG_PCG, g.PCG][i % 3]))
+    s1 = g.Server(max_slots=1, precision=g.MIXED)
+    alone = [s1.wait(submit(g, s1, r)) for r in reqs]
+    s1.close()
+    s4 = g.Server(max_slots=4, precision=g.MIXED)
+    tks = [submit(g, s4, r) for r in reqs]
+    mix = [s4.wait(tk) for tk in tks]
+    s4.close()
+    for i, (r, a, m) in enumerate(zip(reqs, alone, mix)):
+        assert a["status"] == g.ILU_OK and m["status"] == g.ILU_OK, i
+        assert a["rel_res"] <= 1e-8 and a["iters"] == m["iters"], i
+        if r["method"] in (g.MG_VCYCLE, g.MG_PCG):
+            assert a["iters"] <= 8, (i, a["iters"])
+        assert np.array_equal(a["x"], m["x"]), i
+    r, a = reqs[0], alone[0]
+    N = 2 ** r["level"]
+    pr = orc.Problem(r["P"], r["level"], orc.Coeff(*r["co"]))
+    S = orc.to_scipy(pr.A, N)
+    ids, _ = orc.interior_ids(N)
+    inn, bnd = np.nonzero(ids >= 0)[0], np.nonzero(ids < 0)[0]
+    xs = r["x0"].copy()
+    xs[inn] = spla.spsolve(S[inn][:, inn].tocsc(), r["b"][inn] - S[inn][:, bnd] @ r["x0"][bnd])
+    assert np.abs(a["x"] - xs).max() < 1e-6 * np.abs(xs).max()
+    s = g.Server(max_slots=1, precision=g.MIXED)
+    with pytest.raises(g.IluError):
+        s.submit(mesh[0], 2, si.rhs(2, 1), method=g.MG_VCYCLE)
+    s.close()

@@ -41,3 +41,21 @@ def test_requests_without_device_fail_cleanly(g):
     with pytest.raises(ValueError):
         s.submit(si.macro_tet(1), 3, b[:-1])
     s.close()
+
+
+def test_multigrid_request_checks(g):
+    """Multigrid requests need level >= 3; methods beyond the four are
+    rejected at submit; without a device they end with ILU_ENODEV."""
+    torch = pytest.importorskip("torch")
+    s = g.Server(budget_bytes=1e9, max_slots=1) if not torch.cuda.is_available() else None
+    if s is None:
+        pytest.skip("this case needs a machine without a GPU")
+    with pytest.raises(g.IluError) as e:
+        s.submit(si.macro_tet(1), 2, si.rhs(2, 1), method=g.MG_VCYCLE)
+    assert e.value.status == g.ILU_EINVAL
+    with pytest.raises(g.IluError) as e:
+        s.submit(si.macro_tet(1), 3, si.rhs(3, 1), method=4)
+    assert e.value.status == g.ILU_EINVAL
+    tk = s.submit(si.macro_tet(1), 3, si.rhs(3, 1), method=g.MG_PCG, poly_degree=2)
+    assert s.wait(tk, timeout_ms=20000)["status"] == g.ILU_ENODEV
+    s.close()

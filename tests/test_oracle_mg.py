@@ -158,3 +158,41 @@ def test_table2_counts_follow_from_rates(table2):
     for _, _, rg, ri, ng, ni in table2[1]:
         for r, n in [(float(rg), ng), (float(ri), ni)]:
             assert n == int(np.ceil(np.log(1e-6) / np.log(r)))
+
+
+def test_table2_pin_catches_planted_mistakes(orc, mg, table2):
+    """The Table 2 pin is sharp: plausible mistakes planted in the oracle's
+    chain move the Regular tet's rate outside the tolerance the pin allows
+    around the printed 0.025."""
+    shapes, _ = table2
+    P = shapes["regular"]
+    _, nint = orc.interior_ids(64)
+    e0 = np.random.default_rng(5).uniform(-1, 1, nint)
+    tol = printed_tol("0.025", 0.03)
+    exact, _ = mg.Hierarchy(P, 6).rate(e0)
+    assert abs(exact - 0.025) <= tol
+
+    def rate(make):
+        fac = {}
+        for l in range(3, 7):
+            A = orc.assemble(P, 2 ** l)
+            fac[l] = make(A, 2 ** l)
+        return mg.Hierarchy(P, 6, factors=fac).rate(e0)[0]
+
+    def ilu(A, N):
+        L, D = orc.ilu0(A, N)
+        return L, 1.0 / D
+
+    planted = {
+        # the ILU recursion without its correction sums (= symmetric Gauss-Seidel)
+        "dropped correction terms": lambda A, N: (orc.sgs_factors(A, N)[0], 1.0 / orc.sgs_factors(A, N)[1]),
+        # two directions of the factor exchanged (w and s)
+        "transposed directions": lambda A, N: (ilu(A, N)[0][[1, 0, 2, 3, 4, 5, 6]].copy(), ilu(A, N)[1]),
+        # the bc entry of the factor dropped
+        "dropped bc term": lambda A, N: (ilu(A, N)[0] * np.array([1, 1, 1, 1, 1, 0, 1.0])[:, None], ilu(A, N)[1]),
+        # the diagonal off by 10 %
+        "scaled diagonal": lambda A, N: (ilu(A, N)[0], ilu(A, N)[1] / 1.1),
+    }
+    for name, make in planted.items():
+        rho = rate(make)
+        assert abs(rho - 0.025) > tol, (name, rho)

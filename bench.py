@@ -296,6 +296,29 @@ def level9_workload(args, g, torch):
                      "launches_per_step": launches / K}
         t.close()
     f = out[g.F32]
+    # bandwidth scaling: the same F32 sweep at levels 6-8 (slab kernels) and 9 (band kernels)
+    scaling = {}
+    for lv in [6, 7, 8]:
+        t = g.Tet(P, lv, coeff=g.make_coeff("const"), poly_degree=6, precision=g.F32)
+        b = torch.tensor(si.rhs(lv, 6), dtype=torch.float32, device="cuda")
+        x = torch.zeros_like(b)
+        t.smooth(x, b, W)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        tot = 0.0
+        for k in range(K):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.smooth(x, b, 1)
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / K
+        scaling[f"L{lv}"] = {"interior_dof": interior(lv), "ms_per_step": round(ms, 4),
+                             "value": interior(lv) / (ms / 1e3)}
+        t.close()
+        del flush
+    scaling["L9"] = {"interior_dof": nint, "ms_per_step": round(f["ms_per_step"], 4), "value": f["value"]}
     return {"metric": "smoother DoF-sweeps/s (single macro-tet, level 9, FP32 sweeps)", "value": f["value"],
             "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": f["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -308,6 +331,7 @@ def level9_workload(args, g, torch):
             "f64": {"value": out[g.F64]["value"], "ms_per_step": out[g.F64]["ms_per_step"],
                     "achieved_gbs": out[g.F64]["achieved_gbs"], "frac": out[g.F64]["frac"],
                     "kernel_ms_per_launch": out[g.F64]["kernel_ms"]},
+            "f32_level_scaling": scaling,
             "gpu_launches": int(round(f["launches_per_step"] * K))}
 
 
@@ -616,6 +640,26 @@ def main():
              "cycles_per_level": round(sub_ms * 1e-3 / levels * sm_mhz * 1e6),
              "hbm_time_us_per_substitution": round(1e6 * alg["backward"]["bytes"] / (hbm * 1e9), 2)}
 
+    # the same sweep in the other two precisions (timed the same way, after
+    # the headline measurement)
+    prec = {}
+    for name, pp, dt in [("F32", g.F32, torch.float32), ("F64", g.F64, torch.float64)]:
+        tp = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=pp, device=local)
+        bp = torch.tensor(b_h, dtype=dt, device="cuda")
+        xp = torch.zeros(nn, dtype=dt, device="cuda")
+        tp.smooth(xp, bp, W)
+        Kp = max(3, min(K, 50))
+        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Kp)]
+        for k in range(Kp):
+            flush.fill_(float(k))
+            evp[k][0].record(stream)
+            tp.smooth(xp, bp, 1)
+            evp[k][1].record(stream)
+        torch.cuda.synchronize()
+        msp = sum(a.elapsed_time(bb) for a, bb in evp) / Kp
+        prec[name] = {"ms_per_step": round(msp, 5), "value": interior(LEVEL) / (msp / 1e3)}
+        tp.close()
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
@@ -626,6 +670,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof,
             "depth": depth,
+            "other_precisions": prec,
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"]}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

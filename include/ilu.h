@@ -82,7 +82,21 @@ typedef struct {
   int factor;          /* factors the surrogates approximate: an ilu_factor value */
   int stencil;         /* how a variable-kappa operator is applied: an ilu_stencil_mode value */
   int orient;          /* vertex order used: an ilu_orient value */
+  int boundary;        /* boundary variant of the factors: an ilu_boundary value */
 } ilu_opts;
+
+/* The two boundary variants of Sec. 4.1 and Alg. 2:
+ *   ILU_BOUNDARY_V2  surrogates everywhere; a factor entry whose neighbour is
+ *                    not interior is set to 0 in the substitutions (default);
+ *   ILU_BOUNDARY_V1  at the interior points on the cell boundary (x = 1,
+ *                    y = 1, z = 1 or x + y + z = N - 1) the exact ILU(0)
+ *                    entries L^p_d, d in D_l, computed by Alg. 1 at set-up,
+ *                    are stored (7 values per such point, O(N^2) in all) and
+ *                    used instead of the surrogates: by the forward
+ *                    substitution at p, by the backward one wherever p - d
+ *                    is such a point.  D~^-1 stays a surrogate (Alg. 2).
+ *                    Uses the slab substitution kernels. */
+typedef enum { ILU_BOUNDARY_V2 = 0, ILU_BOUNDARY_V1 = 1 } ilu_boundary;
 
 /* Which vertex order of the macro-tetrahedron the handle uses (Sec. 3):
  *   ILU_ORIENT_GIVEN  p1..p4 as passed (default);

@@ -281,6 +281,24 @@ def eval_surrogates(N, deg, coefs):
     return L, Dinv
 
 
+def cell_boundary_mask(N):
+    """Interior points on the cell boundary, in interior order: those with a
+    neighbour in D outside the interior, i.e. x = 1, y = 1, z = 1 or
+    x + y + z = N - 1 (the points whose factors variant V1 stores, Sec. 4.1)."""
+    c = interior_coords(N)
+    return (c[:, 0] == 1) | (c[:, 1] == 1) | (c[:, 2] == 1) | (c.sum(axis=1) == N - 1)
+
+
+def v1_factors(N, L_sur, L_exact):
+    """Boundary variant V1 (Sec. 4.1, Alg. 2): the exact ILU(0) factor at the
+    cell-boundary points, the surrogate elsewhere.  D~^-1 stays the
+    surrogate's.  Alg. 2 applied with this field is the V1 smoother."""
+    m = cell_boundary_mask(N)
+    L = np.array(L_sur, dtype=np.float64, copy=True)
+    L[:, m] = L_exact[:, m]
+    return L
+
+
 # ------------------------------------------------------------ smoother ---
 
 def smooth(A, N, L, Dinv, x, b, sweeps=1, want_norms=False):

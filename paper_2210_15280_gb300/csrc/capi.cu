@@ -61,6 +61,8 @@ struct ilu_tet_s {
   int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO, stencil_choice = ILU_STENCIL_AUTO;
   int perm[4] = {0, 1, 2, 3};  // vertex order used (ILU_ORIENT_LFA)
   double *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa)
+  void *d_bnd = nullptr;       // boundary variant V1: exact factor records (sweep precision)
+  int *d_bnd_off = nullptr;    // and their row offsets
   int band_Z = 8, band_ntiles = 0, band_ncta = 0;
   BandInfo *d_binfo = nullptr;
   int *d_bint = nullptr;  // CTA list, tile list, cluster map {0, ncta, 0}, tile prefix {0, ntiles}, epoch
@@ -102,7 +104,10 @@ void free_device(ilu_tet t) {
   t->ev_used.clear();
   t->ev_pool.clear();
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa); cudaFree(t->d_astore);
+  cudaFree(t->d_bnd); cudaFree(t->d_bnd_off);
   t->d_astore = nullptr;
+  t->d_bnd = nullptr;
+  t->d_bnd_off = nullptr;
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
   cudaFree(t->d_dev); cudaFree(t->d_map); cudaFree(t->d_chunks);
   t->d_dev = nullptr; t->d_map = nullptr; t->d_chunks = nullptr;
@@ -316,7 +321,7 @@ ilu_status upload(ilu_tet t) {
   CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
   // band kernels: measured faster than the slab kernels from level 9 on
   // (L7/L8/L9 MIXED sweeps: 0.78/1.77/10.2 ms slab, 1.10/2.19/6.0 ms band)
-  t->use_band = t->precision != ILU_F64 && wave_uses_registers(t->kind(), h.dx) &&
+  t->use_band = t->precision != ILU_F64 && h.boundary == ILU_BOUNDARY_V2 && wave_uses_registers(t->kind(), h.dx) &&
                 (t->kernel_choice == ILU_KERNEL_BAND || (t->kernel_choice == ILU_KERNEL_AUTO && h.L >= 9));
   if (t->use_band) {
     ilu_status bs = upload_band(t, t->requested_slabs);
@@ -332,6 +337,24 @@ ilu_status upload(ilu_tet t) {
   std::memcpy(d.Wstar, h.Wstar, sizeof(d.Wstar));
   d.astore = nullptr;
   d.astride = (int64_t)nn;
+  d.bnd = nullptr;
+  d.bnd_off = nullptr;
+  if (h.boundary == ILU_BOUNDARY_V1) {
+    const size_t nrec = h.bndL.size() / 8;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    CK(cudaMalloc(&t->d_bnd, std::max<size_t>(nrec, 1) * 8 * es), "cudaMalloc boundary factors");
+    CK(cudaMalloc(&t->d_bnd_off, h.bnd_rowoff.size() * sizeof(int)), "cudaMalloc boundary offsets");
+    if (f64) {
+      if (nrec) CK(cudaMemcpy(t->d_bnd, h.bndL.data(), nrec * 8 * es, cudaMemcpyHostToDevice), "upload boundary factors");
+    } else {
+      std::vector<float> f(h.bndL.begin(), h.bndL.end());
+      if (nrec) CK(cudaMemcpy(t->d_bnd, f.data(), nrec * 8 * es, cudaMemcpyHostToDevice), "upload boundary factors");
+    }
+    CK(cudaMemcpy(t->d_bnd_off, h.bnd_rowoff.data(), h.bnd_rowoff.size() * sizeof(int), cudaMemcpyHostToDevice),
+       "upload boundary offsets");
+    d.bnd = t->d_bnd;
+    d.bnd_off = t->d_bnd_off;
+  }
   if (!h.const_kappa) {
     const size_t abytes = (size_t)(kNumDirs - 1) * nn * sizeof(double);
     const bool store = t->stencil_choice == ILU_STENCIL_STORED ||
@@ -613,6 +636,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->factor = ILU_FACTOR_ILU0;
   o->stencil = ILU_STENCIL_AUTO;
   o->orient = ILU_ORIENT_GIVEN;
+  o->boundary = ILU_BOUNDARY_V2;
   return ILU_OK;
 }
 
@@ -649,6 +673,9 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (o.factor != ILU_FACTOR_ILU0 && o.factor != ILU_FACTOR_SGS) return fail(ILU_EINVAL, "unknown factor choice");
   if (o.stencil < ILU_STENCIL_AUTO || o.stencil > ILU_STENCIL_STORED) return fail(ILU_EINVAL, "unknown stencil choice");
   if (o.orient != ILU_ORIENT_GIVEN && o.orient != ILU_ORIENT_LFA) return fail(ILU_EINVAL, "unknown orientation choice");
+  if (o.boundary != ILU_BOUNDARY_V2 && o.boundary != ILU_BOUNDARY_V1) return fail(ILU_EINVAL, "unknown boundary variant");
+  if (o.boundary == ILU_BOUNDARY_V1 && o.kernel == ILU_KERNEL_BAND)
+    return fail(ILU_EINVAL, "boundary variant V1 runs on the slab kernels");
   int perm[4] = {0, 1, 2, 3};
   if (o.orient == ILU_ORIENT_LFA) {
     ilu_status ls = ilu_lfa_order(macro_tet, perm, nullptr, nullptr);
@@ -669,6 +696,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   ilu_status st;
   try {
     t->host.factor = o.factor;
+    t->host.boundary = o.boundary;
     st = host_setup(t->host, Pv, level, coeff, deg, o.sample_level, o.ridge, err);
   } catch (const std::bad_alloc &) {
     st = ILU_ENOMEM;

@@ -78,6 +78,22 @@ ILU_HD int64_t row_id(int N, int y, int z) {
 // interior x-range of row (y,z) is [1, N-1-y-z]; its centre
 ILU_HD int row_len(int N, int y, int z) { return N - 1 - y - z; }
 
+// ---- boundary variant V1: the interior points on the cell boundary (a
+// neighbour in D outside the interior) keep their exact factors.  Rows with
+// y = 1 or z = 1 lie wholly on it; every other row has its first (x = 1) and
+// last (x + y + z = N - 1) point on it.  Records are numbered in
+// lexicographic order; off[row_id] is the first record of a row.
+ILU_HD bool on_cell_boundary(int N, int x, int y, int z) { return x == 1 || y == 1 || z == 1 || x + y + z == N - 1; }
+ILU_HD int bnd_row_count(int N, int y, int z) {
+  const int n = row_len(N, y, z);
+  return (y == 1 || z == 1) ? n : (n < 2 ? n : 2);
+}
+// record of a cell-boundary point (x, y, z), given the row offsets
+ILU_HD int bnd_record(const int *off, int N, int x, int y, int z) {
+  const int o = off[row_id(N, y, z)];
+  return (y == 1 || z == 1) ? o + x - 1 : o + (x == 1 ? 0 : 1);
+}
+
 // ---- bands: the FP32 sweeps give each lane of a warp one row.  Band k of
 // layer z holds the 32 rows y = band_Y(z,k) + j, j = 0..31 (rows outside
 // [1, N-2-z] are idle lanes).  The bands slant by one row per layer, so that

@@ -58,6 +58,8 @@ struct DevTet {
   const double *astore;  // variable kappa, stored operator: coefficient of direction d (d != centre) of
                          // row p at astore[(d < 7 ? d : d - 1) * astride + p]; null: assembled on the fly
   int64_t astride;
+  const void *bnd;       // boundary variant V1: 8 values per cell-boundary point (sweep precision), or null
+  const int *bnd_off;    // its row offsets (bnd_record in grid.h)
 };
 
 struct LaunchStatus {

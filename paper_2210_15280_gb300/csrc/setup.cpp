@@ -443,6 +443,10 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
           for (int d = 0; d < 7; ++d) t.exactL[(size_t)d * nint + i] = Lp[d];
           t.exactD[i] = Dp;
         }
+        if (t.boundary == ILU_BOUNDARY_V1 && on_cell_boundary(N, x, y, z)) {  // records in lexicographic order
+          for (int d = 0; d < 7; ++d) t.bndL.push_back(Lp[d]);
+          t.bndL.push_back(0.0);
+        }
         for (int f = 0; f < 8; ++f) {
           const int dx = f < 7 ? dir_dx(f) : 0, dy = f < 7 ? dir_dy(f) : 0, dz = f < 7 ? dir_dz(f) : 0;
           if (mod(x - 1 + dx, stride) || mod(y - 1 + dy, stride) || mod(z - 1 + dz, stride)) continue;
@@ -530,6 +534,20 @@ ilu_status host_setup(HostTet &t, const double P[12], int level, const ilu_coeff
       if (!(v > 0) || !std::isfinite(v)) { err = "kappa must be positive and finite at every grid point"; return ILU_EINVAL; }
   }
   t.keep_exact = level <= 7;
+  t.bndL.clear();
+  t.bnd_rowoff.clear();
+  if (t.boundary == ILU_BOUNDARY_V1) {
+    const int64_t rows = num_rows(t.N);
+    t.bnd_rowoff.assign((size_t)rows + 1, 0);
+    int acc = 0;
+    for (int z = 1; z <= t.N - 3; ++z)
+      for (int y = 1; y <= t.N - 2 - z; ++y) {
+        t.bnd_rowoff[(size_t)row_id(t.N, y, z)] = acc;
+        acc += bnd_row_count(t.N, y, z);
+      }
+    t.bnd_rowoff[(size_t)rows] = acc;
+    t.bndL.reserve((size_t)acc * 8);
+  }
   std::vector<Sample> samples[8];
   ilu_status st = factorise(t, samples, err);
   if (st != ILU_OK) return st;

@@ -568,8 +568,17 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
           }
           const TW *rr = rin + (size_t)(s & (IS - 1)) * SS + li * RC;
           // one point of the forward substitution: L holds L~^p_d, d in D_l
-          auto point = [&](int y, const TW(&L)[8]) {
+          const TW *bndv = reinterpret_cast<const TW *>(t.bnd);  // boundary variant V1 (else null)
+          auto point = [&](int y, const TW(&Lin)[8]) {
             const int x = s - 2 * y - 3 * z;
+            TW L[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) L[d] = Lin[d];
+            if (bndv && on_cell_boundary(N, x, y, z)) {  // V1: the stored exact factor at p
+              const TW *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, y, z) * 8;
+#pragma unroll
+              for (int d = 0; d < 7; ++d) L[d] = rec[d];
+            }
             // all operands first, so that their shared-memory latencies
             // overlap; an index outside the row is clamped into it and the
             // value it reads is never used (the V2 tests below skip it)
@@ -813,8 +822,20 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
           const TX *xx = xin + (size_t)(s & (IS - 1)) * SS + li * RC;
           const bool store_w = bottom && k > 0 && !intra_out;  // the next cluster reads this layer
           // one point of the backward substitution: L[0] = 1/D~^p, L[1+d] = L~^{p-d}_d
-          auto point = [&](int y, const TW(&L)[8]) {
+          const TW *bndv = reinterpret_cast<const TW *>(t.bnd);  // boundary variant V1 (else null)
+          auto point = [&](int y, const TW(&Lin)[8]) {
             const int x = s - 2 * y - 3 * z;
+            TW L[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) L[d] = Lin[d];
+            if (bndv) {  // V1: L~^{p-d}_d from the stored exact factor where p - d is on the cell boundary
+#pragma unroll
+              for (int d = 0; d < kNumLower; ++d) {
+                const int qx = x - dir_dx(d), qy = y - dir_dy(d), qz = z - dir_dz(d);
+                if (in_interior(N, qx, qy, qz) && on_cell_boundary(N, qx, qy, qz))
+                  L[1 + d] = bndv[(size_t)bnd_record(t.bnd_off, N, qx, qy, qz) * 8 + d];
+              }
+            }
             // operands first (clamped indices, as in the forward kernel)
             auto in = [&](int i) { return min(max(i, 0), RC - 1); };
             const TW vw0 = ww[y - ylo];

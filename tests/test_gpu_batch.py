@@ -114,3 +114,25 @@ def test_batch_rejects_bad_input(g):
     with pytest.raises(g.IluError):
         b.smooth([x], [None], 1)
     b.smooth([x], [x.clone()], 0)  # no sweeps: nothing to do
+
+
+def test_batch_with_v1_tets_equals_single_sweeps(g):
+    """Tets set up with boundary variant V1 batch like any other (slab
+    kernels; the boundary records travel in each tet's descriptor)."""
+    mesh = si.macro_mesh(8, n_tets=4)
+    tets = []
+    for i, P in enumerate(mesh):
+        co = COEFFS[i % 3]
+        L = [5, 6, 5, 4][i]
+        bnd = g.BOUNDARY_V1 if i % 2 == 0 else g.BOUNDARY_V2
+        tets.append((P, L, 4, co, g.Tet(P, L, coeff=g.make_coeff(*co), poly_degree=4, precision=g.MIXED,
+                                        boundary=bnd)))
+    xs, bs = vectors(tets, torch.float64, 500)
+    ref = [x.clone() for x in xs]
+    for (P, L, d, co, t), x, b in zip(tets, ref, bs):
+        t.smooth(x, b, 2)
+    batch = g.Batch([t for *_, t in tets])
+    batch.smooth(xs, bs, 2)
+    for i, (x, r) in enumerate(zip(xs, ref)):
+        assert torch.equal(x, r), i
+    batch.close()

@@ -159,3 +159,25 @@ def test_lfa_orientation_in_multigrid(g, orc):
             assert m.tet(6).vertex_order() == g.lfa_order(P)[0]
         m.close()
     assert 0.6 < out[g.ORIENT_GIVEN] < 0.7 and 0.36 < out[g.ORIENT_LFA] < 0.42, out
+
+
+def test_v1_vcycle_matches_oracle(g, orc, omg):
+    """A V-cycle whose smoothers all use boundary variant V1."""
+    level = 5
+    P = si.macro_tet(55)
+    co = CO["sinprod"]
+    m = g.Multigrid(P, level, coeff=g.make_coeff(*co), poly_degree=4, nu=3, precision=g.F64,
+                    boundary=g.BOUNDARY_V1)
+    fac = {}
+    for l in range(3, level + 1):
+        pr = orc.Problem(P, l, orc.Coeff(*co), deg=4)
+        m.tet(l).import_surrogate(pr.coefs)
+        Ls, Dinv = pr.surrogate_factors()
+        fac[l] = (orc.v1_factors(pr.N, Ls, pr.L), Dinv)
+    H = omg.Hierarchy(P, level, coeff=orc.Coeff(*co), nu=3, factors=fac)
+    x = si.boundary_data(level, 56)
+    b = si.rhs(level, 57)
+    xo = H.vcycle(level, x.copy(), b)
+    xd = dev(x, torch.float64)
+    m.cycle(xd, dev(b, torch.float64), 1)
+    assert rel(xd.cpu().numpy(), xo) < 1e-12

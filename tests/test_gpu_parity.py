@@ -240,3 +240,28 @@ def test_stored_stencil_bitwise_equals_on_the_fly(g, orc, level, prec, kernel):
     Ls, Dinv = pr.surrogate_factors()
     xo = orc.smooth(pr.A, pr.N, Ls, Dinv, x0.copy(), b, 2)
     assert rel(out[1][0].astype(np.float64), xo) < (1e-12 if p == g.F64 else 2e-5)
+
+
+@pytest.mark.parametrize("level,kind,prec", [(3, "const", "F64"), (4, "sinprod", "F64"), (5, "kappa_i", "F64"),
+                                             (6, "sinprod", "F64"), (5, "sinprod", "MIXED"), (7, "const", "MIXED"),
+                                             (6, "kappa_i", "F32")])
+def test_v1_boundary_variant_matches_oracle(g, orc, level, kind, prec):
+    """Variant V1: exact factors at the cell-boundary points, surrogates
+    elsewhere (the oracle's v1_factors), through the slab kernels."""
+    P, co, pr = problem(orc, level, 80 + level, kind, 4)
+    p = getattr(g, prec)
+    dt = torch.float32 if p == g.F32 else torch.float64
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=4, precision=p, boundary=g.BOUNDARY_V1)
+    t.import_surrogate(pr.coefs)
+    x0 = si.boundary_data(level, 81)
+    b = si.rhs(level, 82)
+    Ls, Dinv = pr.surrogate_factors()
+    xo = orc.smooth(pr.A, pr.N, orc.v1_factors(pr.N, Ls, pr.L), Dinv, x0.copy(), b, 2)
+    xd = dev(x0, dt)
+    t.smooth(xd, dev(b, dt), 2)
+    assert rel(xd.cpu().numpy().astype(np.float64), xo) < (1e-12 if p == g.F64 else 2e-5)
+    # and it differs from V2 where the surrogate misses the boundary factors
+    # (at levels 3 and 4 every point is a sample and the fit is nearly exact)
+    if level >= 5:
+        x2 = orc.smooth(pr.A, pr.N, Ls, Dinv, x0.copy(), b, 2)
+        assert rel(x2, xo) > 1e-9

@@ -517,3 +517,31 @@ def test_exact_ilu_beats_sgs(orc):
         ev = np.linalg.eigvals(np.eye(len(Att)) - np.linalg.solve(C, Att))
         rho.append(np.abs(ev).max())
     assert rho[0] < rho[1] < 1
+
+
+# ----------------------------------------------------- boundary variant ---
+
+@pytest.mark.parametrize("level", [2, 3, 4])
+def test_cell_boundary_mask_is_the_points_with_an_outside_neighbour(orc, level):
+    """V1 (Sec. 4.1): the cell-boundary points are the interior points with a
+    neighbour in D outside the interior; checked by brute force."""
+    N = 2 ** level
+    dirs = [(-1, 0, 0), (0, -1, 0), (1, -1, 0), (-1, 1, -1), (0, 1, -1), (0, 0, -1), (1, 0, -1),
+            (1, 0, 0), (0, 1, 0), (-1, 1, 0), (1, -1, 1), (0, -1, 1), (0, 0, 1), (-1, 0, 1)]
+    inside = lambda x, y, z: x >= 1 and y >= 1 and z >= 1 and x + y + z <= N - 1
+    want = np.array([any(not inside(x + a, y + b, z + c) for a, b, c in dirs)
+                     for x, y, z in orc.interior_coords(N)])
+    assert np.array_equal(orc.cell_boundary_mask(N), want)
+    # O(N^2): every interior point at level 2 and 3, a thin shell above
+    if level == 4:
+        assert want.sum() < 0.75 * len(want)
+
+
+def test_v1_with_exact_factors_is_the_exact_smoother(orc):
+    """With the surrogate replaced by the exact factor, V1 changes nothing."""
+    pr = orc.Problem(si.macro_tet(31), 4)
+    L1 = orc.v1_factors(pr.N, pr.L, pr.L)
+    assert np.array_equal(L1, pr.L)
+    Lx = orc.v1_factors(pr.N, np.zeros_like(pr.L), pr.L)
+    m = orc.cell_boundary_mask(pr.N)
+    assert np.array_equal(Lx[:, m], pr.L[:, m]) and not Lx[:, ~m].any()

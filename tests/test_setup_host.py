@@ -159,3 +159,17 @@ def test_sgs_surrogate_matches_oracle_fit(g, orc):
     got = np.array([t.eval_surrogate(*p) for p in ic[::5]])
     assert np.abs(got[:, :7] - Ls.T[::5]).max() < 1e-8
     assert np.abs(got[:, 7] - Dinv[::5]).max() < 1e-8 * np.abs(Dinv).max()
+
+
+def test_v1_keeps_the_fit_and_rejects_band_kernels(g):
+    """Variant V1 stores boundary factors beside the same surrogate fit; it
+    runs on the slab kernels only."""
+    P = si.macro_tet(33)
+    a = g.Tet(P, 5, poly_degree=4, device=-1)
+    b = g.Tet(P, 5, poly_degree=4, device=-1, boundary=g.BOUNDARY_V1)
+    assert np.array_equal(a.export_surrogate(), b.export_surrogate())
+    with pytest.raises(g.IluError) as e:
+        g.Tet(P, 5, poly_degree=4, device=-1, boundary=g.BOUNDARY_V1, kernel=g.KERNEL_BAND)
+    assert e.value.status == g.ILU_EINVAL
+    with pytest.raises(g.IluError):
+        g.Tet(P, 5, poly_degree=4, device=-1, boundary=5)

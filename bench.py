@@ -38,6 +38,11 @@ Further workloads print a line of the same form (not the default run):
                      solves to 1e-8 by V-cycle iteration and by V-cycle
                      preconditioned CG at levels 5-9, and the convergence
                      factors of the paper's Table 2 shapes measured on the GPU.
+  --workload boundary  convergence factors of the V(3,3)-cycle (levels 2..6)
+                     with boundary variants V1 and V2 across surrogate
+                     degrees: the trirectangular unit tet with kappa_i =
+                     1 + 10(x^i + y^i + z^i), i = 0..3, and a tet of height
+                     0.1 with kappa = 1, isotropic degrees and (0, 0, d).
 """
 import argparse
 import json
@@ -528,6 +533,45 @@ def mg_workload(args, g, torch):
             "levels": levels, "table2_rates_deg7_f64": rates}
 
 
+def boundary_workload(args, g, torch):
+    """Rates of the surrogate-ILU V-cycle with boundary variants V1 and V2
+    against the surrogate degree (Sec. 4.2, the studies on kappa_i and on a
+    flat tet)."""
+    t_start = time.time()
+    e = torch.tensor(si.interior_error(6, 9), dtype=torch.float64, device="cuda")
+
+    def rho(P, coeff, deg, bnd):
+        try:
+            m = g.Multigrid(P, 6, coeff=coeff, poly_degree=0, nu=3, precision=g.F64, deg=deg, boundary=bnd)
+        except g.IluError as err:  # e.g. a low-degree surrogate of 1/D that is not positive
+            return str(err)
+        r, _ = m.rate(e.clone(), 20)
+        m.close()
+        return round(r, 4)
+
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    kappa = {}
+    for i in range(4):
+        co = g.make_coeff("kappa_i", 0.0, 0.0, i)
+        kappa[f"kappa_{i}"] = {f"deg{d}": {"V1": rho(tri, co, d, g.BOUNDARY_V1), "V2": rho(tri, co, d, g.BOUNDARY_V2)}
+                               for d in range(0, 7)}
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 0.1]], float)
+    one = g.make_coeff("const")
+    flat_iso = {f"deg{d}": {"V1": rho(flat, one, d, g.BOUNDARY_V1), "V2": rho(flat, one, d, g.BOUNDARY_V2)}
+                for d in range(0, 7)}
+    flat_z = {f"deg(0,0,{d})": {"V1": rho(flat, one, [0, 0, d], g.BOUNDARY_V1),
+                                "V2": rho(flat, one, [0, 0, d], g.BOUNDARY_V2)} for d in range(0, 9, 2)}
+    v = kappa["kappa_3"]["deg3"]
+    return {"metric": "V(3,3)-cycle convergence factor, surrogate ILU(0), boundary variant V1 (kappa_3, degree 3)",
+            "value": v["V1"], "unit": "rho", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": (time.time() - t_start) * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "trirectangular unit tet and a tet of height 0.1, multigrid levels 2..6, "
+                                   "20-step power iteration, F64", "parallelism": "replicas x1"},
+            "v2_value": v["V2"], "trirectangular_kappa_i": kappa, "height_0.1_isotropic": flat_iso,
+            "height_0.1_z_only": flat_z}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -535,7 +579,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
     ap.add_argument("--requests", type=int, default=300)
     args = ap.parse_args()
@@ -551,7 +595,8 @@ def main():
     if args.workload != "single":
         if rank == 0:
             line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload,
-                    "smoothers": smoothers_workload, "mg": mg_workload}[args.workload](
+                    "smoothers": smoothers_workload, "mg": mg_workload,
+                    "boundary": boundary_workload}[args.workload](
                 args, g, torch)
             print(json.dumps(line), flush=True)
         return

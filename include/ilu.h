@@ -115,12 +115,14 @@ typedef enum { ILU_ORIENT_GIVEN = 0, ILU_ORIENT_LFA = 1 } ilu_orient;
  *                           FP64 flops per point, no storage);
  *   ILU_STENCIL_STORED      assemble the 14 off-diagonal coefficients of
  *                           every interior row once at set-up, in FP64 on the
- *                           device (14 x 8 bytes per grid point), and read
- *                           them in the residual;
+ *                           device (14 x 8 bytes per grid point; FP32 for F32
+ *                           sweeps), and read them in the residual;
  *   ILU_STENCIL_AUTO        stored when that array takes at most 4 GiB
  *                           (level 9 and below), otherwise on the fly.
- * Both give bit-identical residuals: the stored coefficients are the same
- * FP64 sums, applied in the same order. */
+ * In F64 and MIXED both give bit-identical residuals: the stored
+ * coefficients are the same FP64 sums, applied in the same order.  F32
+ * sweeps store the coefficients in FP32 (14 x 4 bytes per point) and apply
+ * them in FP32, the precision of their residual. */
 typedef enum { ILU_STENCIL_AUTO = 0, ILU_STENCIL_ON_THE_FLY = 1, ILU_STENCIL_STORED = 2 } ilu_stencil_mode;
 
 /* Which L D L^T preconditioner the surrogates approximate (Sec. 4.2):

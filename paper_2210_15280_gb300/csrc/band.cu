@@ -675,8 +675,8 @@ __device__ __forceinline__ RowStarts row_starts(int N, int y, int z) {
 }
 
 template <typename TX, typename TR, int OP>
-__device__ __forceinline__ TR residual_at(const DevTet &t, const RowStarts &R, int x, const TX *__restrict__ xv_,
-                                          const TX *__restrict__ b) {
+__device__ __forceinline__ TR residual_at(const DevTet &t, const TR *A15, const RowStarts &R, int x,
+                                          const TX *__restrict__ xv_, const TX *__restrict__ b) {
   const int64_t r0 = R.r0, rs = R.rs, rn = R.rn, rb = R.rb, rbn = R.rbn, rt = R.rt, rts = R.rts;
   TR xv[15];
   xv[0] = (TR)xv_[r0 + x - 1];
@@ -697,7 +697,7 @@ __device__ __forceinline__ TR residual_at(const DevTet &t, const RowStarts &R, i
   TR res = (TR)b[r0 + x];
   if (OP == 0) {
 #pragma unroll
-    for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
+    for (int d = 0; d < 15; ++d) res = fma(-A15[d], xv[d], res);
   } else if (OP == 2) {
     stored_apply(res, t.astore, t.astride, r0 + x, xv);
   } else {
@@ -752,6 +752,10 @@ __global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__
   const TX *xv = xs ? xs[lo] : x1;
   const TX *b = bs ? bs[lo] : b1;
   const int op = t.const_kappa ? 0 : (t.astore ? 2 : 1);
+  // the constant stencil, converted once per block to the residual type
+  __shared__ TR sA15[15];
+  if (threadIdx.x < 15) sA15[threadIdx.x] = (TR)t.A15[threadIdx.x];
+  __syncthreads();
   double acc2 = 0.0;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -762,8 +766,9 @@ __global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__
       const RowStarts R = row_starts(N, y, z);
       if (x >= 1 && x <= N - 1 - y - z) {
         if (MODE == 0)
-          r = op == 0 ? residual_at<TX, TR, 0>(t, R, x, xv, b)
-                      : (op == 2 ? residual_at<TX, TR, 2>(t, R, x, xv, b) : residual_at<TX, TR, 1>(t, R, x, xv, b));
+          r = op == 0 ? residual_at<TX, TR, 0>(t, sA15, R, x, xv, b)
+                      : (op == 2 ? residual_at<TX, TR, 2>(t, sA15, R, x, xv, b)
+                                 : residual_at<TX, TR, 1>(t, sA15, R, x, xv, b));
         else r = (TR)xv[R.r0 + x];
         acc2 += (double)r * (double)r;
       }

@@ -60,7 +60,7 @@ struct ilu_tet_s {
   bool use_band = false;
   int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO, stencil_choice = ILU_STENCIL_AUTO;
   int perm[4] = {0, 1, 2, 3};  // vertex order used (ILU_ORIENT_LFA)
-  double *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa)
+  void *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa; float in F32)
   void *d_bnd = nullptr;       // boundary variant V1: exact factor records (sweep precision)
   int *d_bnd_off = nullptr;    // and their row offsets
   int band_Z = 8, band_ntiles = 0, band_ncta = 0;
@@ -356,12 +356,13 @@ ilu_status upload(ilu_tet t) {
     d.bnd_off = t->d_bnd_off;
   }
   if (!h.const_kappa) {
-    const size_t abytes = (size_t)(kNumDirs - 1) * nn * sizeof(double);
+    const bool a32 = t->precision == ILU_F32;
+    const size_t abytes = (size_t)(kNumDirs - 1) * nn * (a32 ? sizeof(float) : sizeof(double));
     const bool store = t->stencil_choice == ILU_STENCIL_STORED ||
                        (t->stencil_choice == ILU_STENCIL_AUTO && abytes <= ((size_t)4 << 30));
     if (store) {
       CK(cudaMalloc(&t->d_astore, abytes), "cudaMalloc stored stencils");
-      CK(launch_stencil_store(d, t->d_astore, cudaStreamPerThread), "stencil assembly launch");
+      CK(launch_stencil_store(d, t->d_astore, a32, cudaStreamPerThread), "stencil assembly launch");
       CK(cudaStreamSynchronize(cudaStreamPerThread), "stencil assembly");
       d.astore = t->d_astore;
     }

@@ -33,7 +33,7 @@ namespace {
 // weights and kappa at the grid points
 struct StencilData {
   const double *A15, *Wstar, *kappa;
-  const double *astore;  // stored off-diagonal coefficients (MODE 2)
+  const void *astore;  // stored off-diagonal coefficients (MODE 2)
   int64_t astride;
 };
 
@@ -80,8 +80,9 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, in
     xv[14] = (TR)x[rt + xx - 1];
     TR res = (TR)b[r0 + xx];
     if (MODE == kOpConst) {
+      const TR *A15 = reinterpret_cast<const TR *>(t.A15);  // the block's copy in the residual type
 #pragma unroll
-      for (int d = 0; d < 15; ++d) res = fma(-(TR)t.A15[d], xv[d], res);
+      for (int d = 0; d < 15; ++d) res = fma(-A15[d], xv[d], res);
     } else if (MODE == kOpStored) {
       stored_apply(res, t.astore, t.astride, r0 + xx, xv);
     } else {
@@ -117,7 +118,11 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
                                                        const TX *__restrict__ b, TW *__restrict__ r,
                                                        double *__restrict__ partials) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const StencilData sd{t.A15, t.Wstar, t.kappa, t.astore, t.astride};
+  // the constant stencil, converted once per block to the residual type
+  __shared__ TR sA15[15];
+  if (threadIdx.x < 15) sA15[threadIdx.x] = (TR)t.A15[threadIdx.x];
+  __syncthreads();
+  const StencilData sd{reinterpret_cast<const double *>(sA15), t.Wstar, t.kappa, t.astore, t.astride};
   const int ci = blockIdx.x * 8 + warp;
   double acc2 = 0.0;
   if (ci < t.nchunks) {
@@ -154,9 +159,10 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
   const DevTet &tg = tets[lo];
   // the block's stencil weights in shared memory (reading them from the
   // device array would keep all 100 live in registers)
-  __shared__ double sW[kStarPairs], sA[15];
+  __shared__ double sW[kStarPairs];
+  __shared__ TR sA[15];
   for (int i = threadIdx.x; i < kStarPairs; i += blockDim.x) sW[i] = tg.Wstar[i];
-  if (threadIdx.x < 15) sA[threadIdx.x] = tg.A15[threadIdx.x];
+  if (threadIdx.x < 15) sA[threadIdx.x] = (TR)tg.A15[threadIdx.x];
   __syncthreads();
   const int N = tg.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
   if (ci >= tg.nchunks) return;  // no block-wide synchronisation follows
   const int ch = tg.chunks[ci];
   TW *r = reinterpret_cast<TW *>(tg.w);
-  const StencilData sd{sA, sW, tg.kappa, tg.astore, tg.astride};
+  const StencilData sd{reinterpret_cast<const double *>(sA), sW, tg.kappa, tg.astore, tg.astride};
   const int y = (ch >> 10) & 1023, z = ch >> 20, x0 = 1 + 32 * (ch & 1023);
   if (tg.const_kappa)
     residual_chunk<TX, TR, TW, kOpConst>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
@@ -329,7 +335,8 @@ cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n,
 
 namespace {
 // one warp per 32-point row chunk, as the residual
-__global__ void __launch_bounds__(256) stencil_store_kernel(DevTet t, double *__restrict__ A) {
+template <typename TA>
+__global__ void __launch_bounds__(256) stencil_store_kernel(DevTet t, TA *__restrict__ A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ci = blockIdx.x * 8 + warp;
   if (ci >= t.nchunks) return;
@@ -360,11 +367,14 @@ __global__ void __launch_bounds__(256) stencil_store_kernel(DevTet t, double *__
 }
 }  // namespace
 
-cudaError_t launch_stencil_store(const DevTet &t, double *A, cudaStream_t st) {
+cudaError_t launch_stencil_store(const DevTet &t, void *A, bool f32, cudaStream_t st) {
   if (t.const_kappa || !t.kappa || !t.chunks) return cudaErrorInvalidValue;
   const int nb = (t.nchunks + 7) / 8;
   if (nb == 0) return cudaSuccess;
-  stencil_store_kernel<<<nb, 256, 0, st>>>(t, A);
+  if (f32)
+    stencil_store_kernel<float><<<nb, 256, 0, st>>>(t, static_cast<float *>(A));
+  else
+    stencil_store_kernel<double><<<nb, 256, 0, st>>>(t, static_cast<double *>(A));
   return cudaGetLastError();
 }
 

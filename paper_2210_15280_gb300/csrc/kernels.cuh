@@ -55,8 +55,9 @@ struct DevTet {
   BandDev band;      // FP32 band sweeps (null info when not used)
   const int *chunks; // residual work list: z << 20 | y << 10 | chunk (32 points of a row)
   int nchunks;
-  const double *astore;  // variable kappa, stored operator: coefficient of direction d (d != centre) of
-                         // row p at astore[(d < 7 ? d : d - 1) * astride + p]; null: assembled on the fly
+  const void *astore;    // variable kappa, stored operator: coefficient of direction d (d != centre) of
+                         // row p at astore[(d < 7 ? d : d - 1) * astride + p], double (float in F32
+                         // sweeps); null: assembled on the fly
   int64_t astride;
   const void *bnd;       // boundary variant V1: 8 values per cell-boundary point (sweep precision), or null
   const int *bnd_off;    // its row offsets (bnd_record in grid.h)
@@ -84,7 +85,7 @@ cudaError_t launch_norm_finish(const double *partials, int n, double *out, cudaS
 // assemble the 14 off-diagonal coefficients of every interior row (variable
 // kappa) into A (14 planes of t.astride doubles), the values the on-the-fly
 // residual computes
-cudaError_t launch_stencil_store(const DevTet &t, double *A, cudaStream_t st);
+cudaError_t launch_stencil_store(const DevTet &t, void *A, bool f32, cudaStream_t st);
 
 // Clusters of a substitution launch handed out as tickets: tets in `order`,
 // tet order[j] taking tickets [prefix[j], prefix[j+1]) in dependency order.

@@ -46,22 +46,32 @@ __device__ __forceinline__ double star_coeff(const double *kq, const double *W) 
 // plane of direction d in the stored operator (the centre has none)
 ILU_HDC int store_plane(int d) { return d < kCentre ? d : d - 1; }
 
-template <int... D>
+template <typename TA, int... D>
 __device__ __forceinline__ void star_store_all(std::integer_sequence<int, D...>, const double *kq, const double *W,
-                                               double *A, int64_t stride, int64_t i) {
-  ((D != kCentre ? (void)(A[store_plane(D) * stride + i] = star_coeff<D>(kq, W)) : (void)0), ...);
+                                               TA *A, int64_t stride, int64_t i) {
+  ((D != kCentre ? (void)(A[store_plane(D) * stride + i] = (TA)star_coeff<D>(kq, W)) : (void)0), ...);
 }
 
-// the same application as star_apply_all with coefficients read from the
-// stored planes: identical operands, identical order, identical result
-template <typename TR>
-__device__ __forceinline__ void stored_apply(TR &res, const double *__restrict__ A, int64_t stride, int64_t i,
-                                             const TR *xv) {
-  const double xc = (double)xv[kCentre];
+// FP64 residuals (F64, MIXED): the same application as star_apply_all with
+// the coefficients read from the stored planes, so identical operands in
+// identical order give an identical result.  FP32 residuals (F32 sweeps):
+// FP32 planes and FP32 arithmetic, the precision those sweeps work in.
+__device__ __forceinline__ void stored_apply(double &res, const void *Av, int64_t stride, int64_t i, const double *xv) {
+  const double *__restrict__ A = static_cast<const double *>(Av);
+  const double xc = xv[kCentre];
 #pragma unroll
   for (int d = 0; d < kNumDirs; ++d) {
     if (d == kCentre) continue;
-    res = (TR)fma(-A[store_plane(d) * stride + i], (double)xv[d] - xc, (double)res);
+    res = fma(-A[store_plane(d) * stride + i], xv[d] - xc, res);
+  }
+}
+__device__ __forceinline__ void stored_apply(float &res, const void *Av, int64_t stride, int64_t i, const float *xv) {
+  const float *__restrict__ A = static_cast<const float *>(Av);
+  const float xc = xv[kCentre];
+#pragma unroll
+  for (int d = 0; d < kNumDirs; ++d) {
+    if (d == kCentre) continue;
+    res = fmaf(-A[store_plane(d) * stride + i], xv[d] - xc, res);
   }
 }
 

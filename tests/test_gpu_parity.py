@@ -217,9 +217,10 @@ def test_sgs_smoother_matches_oracle(g, orc, prec, kernel):
 
 @pytest.mark.parametrize("level,prec,kernel", [(4, "F64", 0), (6, "MIXED", 1), (6, "F32", 2), (5, "MIXED", 2)])
 def test_stored_stencil_bitwise_equals_on_the_fly(g, orc, level, prec, kernel):
-    """ilu_opts.stencil: the stored coefficients are the on-the-fly FP64 sums
-    applied in the same order, so sweeps and residuals agree bit for bit; both
-    match the oracle."""
+    """ilu_opts.stencil: in FP64 residuals (F64, MIXED) the stored
+    coefficients are the on-the-fly FP64 sums applied in the same order, so
+    sweeps and residuals agree bit for bit; F32 sweeps store and apply them in
+    FP32.  All match the oracle."""
     P, co, pr = problem(orc, level, 70 + level, "sinprod", 4)
     p = getattr(g, prec)
     dt = torch.float32 if p == g.F32 else torch.float64
@@ -235,8 +236,11 @@ def test_stored_stencil_bitwise_equals_on_the_fly(g, orc, level, prec, kernel):
         t.smooth(xd, bd, 2)
         out.append((xd.cpu().numpy(), r.cpu().numpy(), rn))
         t.close()
-    assert np.array_equal(out[0][0], out[1][0])
-    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+    if p == g.F32:
+        assert rel(out[1][0], out[0][0]) < 1e-6 and rel(out[1][1], out[0][1]) < 1e-5
+    else:
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
     Ls, Dinv = pr.surrogate_factors()
     xo = orc.smooth(pr.A, pr.N, Ls, Dinv, x0.copy(), b, 2)
     assert rel(out[1][0].astype(np.float64), xo) < (1e-12 if p == g.F64 else 2e-5)

@@ -208,6 +208,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     for (int i : G.members) {
       const DevTet &d = b->dev[i];
       const TetView &v = b->views[i];
+      L.v1 = L.v1 || d.bnd != nullptr;
       L.block_f = std::max(L.block_f, (d.fwd.zb * d.fwd.wpl + 1) * 32);
       L.block_b = std::max(L.block_b, (d.bwd.zb * d.bwd.wpl + 1) * 32);
       L.smem_f = std::max(L.smem_f, wave_smem_bytes(v.N, d.fwd, b->kind, v.rstride, G.reg < 0 ? 99 : G.reg, true));

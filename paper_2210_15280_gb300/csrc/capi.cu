@@ -173,6 +173,7 @@ ilu_status choose_clusters(ilu_tet t) {
   L.kind = t->kind();
   L.reg = wave_uses_registers(L.kind, h.dx) ? h.dx : -1;
   L.dxp = h.rstride;
+  L.v1 = h.boundary == ILU_BOUNDARY_V1;
   L.block_f = (d.fwd.zb * d.fwd.wpl + 1) * 32;
   L.block_b = (d.bwd.zb * d.bwd.wpl + 1) * 32;
   L.smem_f = wave_smem_bytes(h.N, d.fwd, L.kind, h.rstride, h.dx, true);

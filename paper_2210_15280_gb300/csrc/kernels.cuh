@@ -114,6 +114,7 @@ struct WaveLaunch {
   int csize_f, csize_b;    // CTAs per cluster
   int clusters_f, clusters_b;
   int maxP_f, maxP_b;      // most slabs of any tet
+  bool v1;                 // some tet uses boundary variant V1 (its stored factors are consulted)
 };
 
 // Cluster sizes the launchers consider, largest first.

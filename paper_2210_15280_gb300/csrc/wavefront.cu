@@ -413,7 +413,7 @@ __device__ __forceinline__ int ticket_owner(const BatchMap &bm, int ticket) {
 // REG >= 0: FP32 path with the row polynomials (degree REG) in registers,
 // each row pinned to one lane for its whole life; REG < 0: polynomials read
 // from the shared row cache at every point.
-template <typename TW, int DXP, int REG>
+template <typename TW, int DXP, int REG, bool V1>
 __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *__restrict__ tets, BatchMap bm,
                                                                    LaunchStatus *status, long long max_spins) {
   constexpr int NF = 7;
@@ -568,16 +568,19 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
           }
           const TW *rr = rin + (size_t)(s & (IS - 1)) * SS + li * RC;
           // one point of the forward substitution: L holds L~^p_d, d in D_l
-          const TW *bndv = reinterpret_cast<const TW *>(t.bnd);  // boundary variant V1 (else null)
+          // boundary variant V1 (instantiated only for launches with such tets)
+          const TW *bndv = V1 ? reinterpret_cast<const TW *>(t.bnd) : nullptr;
           auto point = [&](int y, const TW(&Lin)[8]) {
             const int x = s - 2 * y - 3 * z;
             TW L[8];
 #pragma unroll
             for (int d = 0; d < 8; ++d) L[d] = Lin[d];
-            if (bndv && on_cell_boundary(N, x, y, z)) {  // V1: the stored exact factor at p
-              const TW *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, y, z) * 8;
+            if constexpr (V1) {
+              if (bndv && on_cell_boundary(N, x, y, z)) {  // the stored exact factor at p
+                const TW *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, y, z) * 8;
 #pragma unroll
-              for (int d = 0; d < 7; ++d) L[d] = rec[d];
+                for (int d = 0; d < 7; ++d) L[d] = rec[d];
+              }
             }
             // all operands first, so that their shared-memory latencies
             // overlap; an index outside the row is clamped into it and the
@@ -658,7 +661,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
 
 // -------------------------------------------------------------- backward --
 
-template <typename TW, typename TX, int DXP, int REG>
+template <typename TW, typename TX, int DXP, int REG, bool V1>
 __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *__restrict__ tets, BatchMap bm,
                                                                    LaunchStatus *status, long long max_spins) {
   constexpr int NF = 8;
@@ -822,13 +825,13 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
           const TX *xx = xin + (size_t)(s & (IS - 1)) * SS + li * RC;
           const bool store_w = bottom && k > 0 && !intra_out;  // the next cluster reads this layer
           // one point of the backward substitution: L[0] = 1/D~^p, L[1+d] = L~^{p-d}_d
-          const TW *bndv = reinterpret_cast<const TW *>(t.bnd);  // boundary variant V1 (else null)
+          const TW *bndv = V1 ? reinterpret_cast<const TW *>(t.bnd) : nullptr;
           auto point = [&](int y, const TW(&Lin)[8]) {
             const int x = s - 2 * y - 3 * z;
             TW L[8];
 #pragma unroll
             for (int d = 0; d < 8; ++d) L[d] = Lin[d];
-            if (bndv) {  // V1: L~^{p-d}_d from the stored exact factor where p - d is on the cell boundary
+            if (V1 && bndv) {  // L~^{p-d}_d from the stored exact factor where p - d is on the cell boundary
 #pragma unroll
               for (int d = 0; d < kNumLower; ++d) {
                 const int qx = x - dir_dx(d), qy = y - dir_dy(d), qz = z - dir_dz(d);
@@ -980,12 +983,14 @@ cudaError_t cluster_launch(K kernel, const WaveLaunch &L, bool fwd, cudaStream_t
 
 template <typename TW, int DXP, int REG>
 cudaError_t fwd_launch(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st, int *query) {
-  return cluster_launch(fwd_wave<TW, DXP, REG>, L, true, st, query, status, max_spins);
+  if (L.v1) return cluster_launch(fwd_wave<TW, DXP, REG, true>, L, true, st, query, status, max_spins);
+  return cluster_launch(fwd_wave<TW, DXP, REG, false>, L, true, st, query, status, max_spins);
 }
 
 template <typename TW, typename TX, int DXP, int REG>
 cudaError_t bwd_launch(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st, int *query) {
-  return cluster_launch(bwd_wave<TW, TX, DXP, REG>, L, false, st, query, status, max_spins);
+  if (L.v1) return cluster_launch(bwd_wave<TW, TX, DXP, REG, true>, L, false, st, query, status, max_spins);
+  return cluster_launch(bwd_wave<TW, TX, DXP, REG, false>, L, false, st, query, status, max_spins);
 }
 
 // FP32 dispatch on the register degree; rows of degree <= 3 are stored with

@@ -726,9 +726,11 @@ __device__ __forceinline__ TR residual_at(const DevTet &t, const TR *A15, const 
 // Tile = 32 steps of one band: each warp computes 4 rows along x (coalesced
 // reads of x, b, kappa), the tile is transposed in shared memory and stored
 // as 32 band lines.  MODE 0: r = b - A x (with the tile's ||r||^2), MODE 1:
-// copy of a full-grid vector into the band array.
+// copy of a full-grid vector into the band array.  Four CTAs per SM (at most
+// 64 registers): the kernel waits on its loads, and the extra warps halve its
+// time at level 9 against two CTAs per SM.
 template <typename TX, typename TR, int MODE>
-__global__ void __launch_bounds__(256) band_in_kernel(const DevTet *__restrict__ tets, const int *__restrict__ tprefix,
+__global__ void __launch_bounds__(256, 4) band_in_kernel(const DevTet *__restrict__ tets, const int *__restrict__ tprefix,
                                                       int ntets, const TX *const *__restrict__ xs,
                                                       const TX *const *__restrict__ bs, const TX *x1, const TX *b1,
                                                       double *__restrict__ partials) {

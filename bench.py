@@ -351,7 +351,7 @@ def serve_workload(args, g, torch):
     levels = si.batch_levels(11, nreq, lo, hi)
     kinds = [("const", 1.0, 0.0, 0), ("sinprod", 1.0, 0.5, 0), ("kappa_i", 0.0, 0.0, 2)]
     which = si.splitmix64(12, nreq) % len(pool)
-    arrivals = si.poisson_arrivals(13, nreq, 0.5e-3)  # seconds from the first submit
+    arrivals = si.poisson_arrivals(13, nreq, args.gap_ms * 1e-3)  # seconds from the first submit
     method = g.PCG if pcg else (g.MG_VCYCLE if mg else g.RICHARDSON)
     reqs = []
     for i in range(nreq):
@@ -402,7 +402,7 @@ def serve_workload(args, g, torch):
             "unit": "solves/s", "n_gpus": 1, "steps": nreq, "warmup": len(warm), "ms_per_step": 1e3 * wall / nreq,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{nreq} Poisson-arrival requests (mean gap 0.5 ms), levels {lo}-{hi}, "
+            "config": {"workload": f"{nreq} Poisson-arrival requests (mean gap {args.gap_ms:g} ms), levels {lo}-{hi}, "
                                    f"{'PCG' if pcg else ('V(3,3) multigrid' if mg else 'Richardson')} to 1e-8, "
                                    "MIXED, 32 macro-tets x 3 kappa",
                        "parallelism": "replicas x1"},
@@ -582,6 +582,7 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
     ap.add_argument("--requests", type=int, default=300)
+    ap.add_argument("--gap-ms", type=float, default=0.5, help="mean gap of the Poisson arrivals (serve)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -368,6 +368,8 @@ typedef struct {
   int max_iter;
   const double *b;   /* host, full grid, ilu_num_nodes(level) doubles; copied on submit */
   const double *x0;  /* host, nullable (zeros): start vector and Dirichlet data */
+  int orient;        /* ilu_orient of the set-up (ILU_ORIENT_LFA: b, x0 and x in the reordered layout) */
+  int boundary;      /* ilu_boundary of the set-up */
 } ilu_request;
 
 typedef struct {

@@ -66,7 +66,8 @@ class ServerOpts(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("macro_tet", ctypes.c_double * 12), ("level", ctypes.c_int), ("coeff", Coeff),
                 ("poly_degree", ctypes.c_int), ("method", ctypes.c_int), ("rtol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("b", ctypes.c_void_p), ("x0", ctypes.c_void_p)]
+                ("max_iter", ctypes.c_int), ("b", ctypes.c_void_p), ("x0", ctypes.c_void_p),
+                ("orient", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -441,12 +442,13 @@ class Server:
             pass
 
     def submit(self, macro_tet, level, b, coeff=None, poly_degree=4, method=RICHARDSON, rtol=1e-8,
-               max_iter=10000, x0=None):
+               max_iter=10000, x0=None, orient=ORIENT_GIVEN, boundary=BOUNDARY_V2):
         r = Request()
         r.macro_tet[:] = [float(v) for v in np.asarray(macro_tet, dtype=np.float64).reshape(12)]
         r.level = int(level)
         r.coeff = coeff if coeff is not None else make_coeff()
         r.poly_degree, r.method, r.rtol, r.max_iter = int(poly_degree), int(method), float(rtol), int(max_iter)
+        r.orient, r.boundary = int(orient), int(boundary)
         bb = np.ascontiguousarray(b, dtype=np.float64)
         xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
         if bb.size != num_nodes(level) or (xx is not None and xx.size != num_nodes(level)):

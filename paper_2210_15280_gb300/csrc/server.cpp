@@ -59,7 +59,7 @@ ilu_status fail(ilu_status s, const std::string &msg) {
 // identity of a set-up tet
 struct Key {
   double P[12];
-  int level, kind, ipow, degree, mg;
+  int level, kind, ipow, degree, mg, orient, boundary;
   double c0, amp;
   bool operator<(const Key &o) const {
     int c = std::memcmp(P, o.P, sizeof(P));
@@ -69,6 +69,8 @@ struct Key {
     if (ipow != o.ipow) return ipow < o.ipow;
     if (degree != o.degree) return degree < o.degree;
     if (mg != o.mg) return mg < o.mg;
+    if (orient != o.orient) return orient < o.orient;
+    if (boundary != o.boundary) return boundary < o.boundary;
     c = std::memcmp(&c0, &o.c0, sizeof(double));
     if (c) return c < 0;
     return std::memcmp(&amp, &o.amp, sizeof(double)) < 0;
@@ -314,6 +316,8 @@ void ilu_server_s::slot_main() {
       ilu_opts_default(&o);
       o.precision = opts.precision;
       o.device = opts.device;
+      o.orient = j.req.orient;
+      o.boundary = j.req.boundary;
       if (j.key.mg)
         s = ilu_mg_setup(j.req.macro_tet, j.req.level, &j.req.coeff, j.req.poly_degree, 3, &o, &t.m);
       else
@@ -405,6 +409,8 @@ ilu_status ilu_server_submit(ilu_server s, const ilu_request *req, uint64_t *tic
   if (req->method < ILU_RICHARDSON || req->method > ILU_MG_PCG) return fail(ILU_EINVAL, "unknown method");
   const bool mg = req->method == ILU_MG_VCYCLE || req->method == ILU_MG_PCG;
   if (mg && req->level < 3) return fail(ILU_EINVAL, "multigrid needs level >= 3");
+  if (req->orient != ILU_ORIENT_GIVEN && req->orient != ILU_ORIENT_LFA) return fail(ILU_EINVAL, "unknown orientation");
+  if (req->boundary != ILU_BOUNDARY_V2 && req->boundary != ILU_BOUNDARY_V1) return fail(ILU_EINVAL, "unknown boundary variant");
   if (!(req->rtol >= 0.0) || req->max_iter < 0) return fail(ILU_EINVAL, "bad tolerance or iteration limit");
   if (req->poly_degree < 0 || req->poly_degree > 12) return fail(ILU_EINVAL, "degree out of [0, 12]");
   const size_t nn = num_nodes(req->level);
@@ -427,6 +433,8 @@ ilu_status ilu_server_submit(ilu_server s, const ilu_request *req, uint64_t *tic
   j.key.amp = req->coeff.amp;
   j.key.degree = req->poly_degree;
   j.key.mg = mg ? 1 : 0;
+  j.key.orient = req->orient;
+  j.key.boundary = req->boundary;
   const size_t ex = s->opts.precision == ILU_F32 ? 4 : 8;
   j.vec_bytes = 2 * nn * ex;
   const bool var = req->coeff.kind != ILU_COEFF_CONST;

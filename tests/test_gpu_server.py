@@ -145,3 +145,34 @@ def test_multigrid_requests(g, orc):
     with pytest.raises(g.IluError):
         s.submit(mesh[0], 2, si.rhs(2, 1), method=g.MG_VCYCLE)
     s.close()
+
+
+def test_requests_with_lfa_order_and_v1(g, orc):
+    """A request may set the vertex order (LFA) and boundary variant of its
+    set-up; its vectors then live in the layout of the reordered tet, and the
+    result equals a standalone solve set up the same way."""
+    P = np.array([[0, 0, 0.5], [0, 0, -0.5], [0.5, 10, 0], [-0.5, 10, 0]])
+    perm = g.lfa_order(P)[0]
+    assert perm != [0, 1, 2, 3]
+    L = 5
+    b = si.rhs(L, 990)
+    s = g.Server(max_slots=2, precision=g.MIXED)
+    tk = s.submit(P, L, b, poly_degree=5, method=g.MG_VCYCLE, rtol=1e-8, max_iter=50,
+                  orient=g.ORIENT_LFA, boundary=g.BOUNDARY_V1)
+    r = s.wait(tk)
+    s.close()
+    assert r["status"] == g.ILU_OK and r["rel_res"] <= 1e-8
+    m = g.Multigrid(P, L, poly_degree=5, nu=3, precision=g.MIXED, orient=g.ORIENT_LFA, boundary=g.BOUNDARY_V1)
+    x = torch.zeros(si.num_nodes(L), dtype=torch.float64, device="cuda")
+    it, rel, ok = m.solve(x, torch.tensor(b, dtype=torch.float64, device="cuda"), g.RICHARDSON, 1e-8, 50)
+    m.close()
+    assert ok and it == r["iters"] and np.array_equal(x.cpu().numpy(), r["x"])
+    # the solution of the reordered tet's assembled system
+    Q = P[perm]
+    N = 2 ** L
+    S = orc.to_scipy(orc.assemble(Q, N), N)
+    ids, _ = orc.interior_ids(N)
+    inn = np.nonzero(ids >= 0)[0]
+    xs = np.zeros_like(b)
+    xs[inn] = spla.spsolve(S[inn][:, inn].tocsc(), b[inn])
+    assert np.abs(r["x"] - xs).max() < 1e-6 * np.abs(xs).max()

@@ -59,3 +59,15 @@ def test_multigrid_request_checks(g):
     tk = s.submit(si.macro_tet(1), 3, si.rhs(3, 1), method=g.MG_PCG, poly_degree=2)
     assert s.wait(tk, timeout_ms=20000)["status"] == g.ILU_ENODEV
     s.close()
+
+
+def test_request_option_checks(g):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("this case needs a machine without a GPU")
+    s = g.Server(budget_bytes=1e9, max_slots=1)
+    for kw in [dict(orient=5), dict(boundary=3)]:
+        with pytest.raises(g.IluError) as e:
+            s.submit(si.macro_tet(1), 3, si.rhs(3, 1), **kw)
+        assert e.value.status == g.ILU_EINVAL
+    s.close()

@@ -26,13 +26,11 @@ namespace {
 
 // --------------------------------------------------------------- residual --
 
-// r = b - A x at the interior points of row (y, z), one warp; returns this
-// lane's share of ||r||^2.  A15/Wstar/kappa come from t (kernel parameter or
-// device memory).
-// where a row's operator comes from: the constant stencil, the edge-star
-// weights and kappa at the grid points
+// Where a row's operator comes from: the constant stencil, or the edge-star
+// weights and kappa at the grid points, or the stored coefficients.
 struct StencilData {
-  const double *A15, *Wstar, *kappa;
+  const void *A15;     // the constant stencil in the residual type (a per-block copy)
+  const double *Wstar, *kappa;
   const void *astore;  // stored off-diagonal coefficients (MODE 2)
   int64_t astride;
 };
@@ -80,7 +78,7 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, in
     xv[14] = (TR)x[rt + xx - 1];
     TR res = (TR)b[r0 + xx];
     if (MODE == kOpConst) {
-      const TR *A15 = reinterpret_cast<const TR *>(t.A15);  // the block's copy in the residual type
+      const TR *A15 = static_cast<const TR *>(t.A15);
 #pragma unroll
       for (int d = 0; d < 15; ++d) res = fma(-A15[d], xv[d], res);
     } else if (MODE == kOpStored) {
@@ -122,7 +120,7 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
   __shared__ TR sA15[15];
   if (threadIdx.x < 15) sA15[threadIdx.x] = (TR)t.A15[threadIdx.x];
   __syncthreads();
-  const StencilData sd{reinterpret_cast<const double *>(sA15), t.Wstar, t.kappa, t.astore, t.astride};
+  const StencilData sd{sA15, t.Wstar, t.kappa, t.astore, t.astride};
   const int ci = blockIdx.x * 8 + warp;
   double acc2 = 0.0;
   if (ci < t.nchunks) {
@@ -170,7 +168,7 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
   if (ci >= tg.nchunks) return;  // no block-wide synchronisation follows
   const int ch = tg.chunks[ci];
   TW *r = reinterpret_cast<TW *>(tg.w);
-  const StencilData sd{reinterpret_cast<const double *>(sA), sW, tg.kappa, tg.astore, tg.astride};
+  const StencilData sd{sA, sW, tg.kappa, tg.astore, tg.astride};
   const int y = (ch >> 10) & 1023, z = ch >> 20, x0 = 1 + 32 * (ch & 1023);
   if (tg.const_kappa)
     residual_chunk<TX, TR, TW, kOpConst>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);

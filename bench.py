@@ -361,7 +361,7 @@ def serve_workload(args, g, torch):
     warm = {}
     for r in reqs:
         warm.setdefault((id(r["P"]), r["level"], r["co"]), r)
-    s = g.Server(precision=g.MIXED, max_slots=64)
+    s = g.Server(precision=g.MIXED, max_slots=64, max_cluster=args.max_cluster)
     for tk in [s.submit(r["P"], r["level"], r["b"], coeff=g.make_coeff(*r["co"]), poly_degree=5, method=method)
                for r in warm.values()]:
         s.wait(tk)
@@ -402,7 +402,8 @@ def serve_workload(args, g, torch):
             "unit": "solves/s", "n_gpus": 1, "steps": nreq, "warmup": len(warm), "ms_per_step": 1e3 * wall / nreq,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"{nreq} Poisson-arrival requests (mean gap {args.gap_ms:g} ms), levels {lo}-{hi}, "
+            "config": {"max_cluster": args.max_cluster,
+                       "workload": f"{nreq} Poisson-arrival requests (mean gap {args.gap_ms:g} ms), levels {lo}-{hi}, "
                                    f"{'PCG' if pcg else ('V(3,3) multigrid' if mg else 'Richardson')} to 1e-8, "
                                    "MIXED, 32 macro-tets x 3 kappa",
                        "parallelism": "replicas x1"},
@@ -583,6 +584,7 @@ def main():
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--gap-ms", type=float, default=0.5, help="mean gap of the Poisson arrivals (serve)")
+    ap.add_argument("--max-cluster", type=int, default=0, help="CTAs per cluster cap of the served set-ups")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -83,6 +83,9 @@ typedef struct {
   int stencil;         /* how a variable-kappa operator is applied: an ilu_stencil_mode value */
   int orient;          /* vertex order used: an ilu_orient value */
   int boundary;        /* boundary variant of the factors: an ilu_boundary value */
+  int max_cluster;     /* at most this many CTAs per cluster in the slab kernels; <=0: the largest the
+                        * device schedules (lowest latency for one tet; smaller clusters pack more
+                        * concurrent tets onto the GPU) */
 } ilu_opts;
 
 /* The two boundary variants of Sec. 4.1 and Alg. 2:
@@ -356,6 +359,7 @@ typedef struct {
   int max_slots;           /* requests on the device at once; <=0: 64 */
   int device;
   int precision;           /* ilu_precision for admitted work */
+  int max_cluster;         /* ilu_opts.max_cluster of the requests' set-ups; <=0: the library default */
 } ilu_server_opts;
 
 typedef struct {

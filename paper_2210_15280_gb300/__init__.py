@@ -55,12 +55,13 @@ class Opts(ctypes.Structure):
     _fields_ = [("deg", ctypes.c_int * 3), ("sample_level", ctypes.c_int), ("ridge", ctypes.c_double),
                 ("precision", ctypes.c_int), ("slabs", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_wait_spins", ctypes.c_longlong), ("kernel", ctypes.c_int), ("factor", ctypes.c_int),
-                ("stencil", ctypes.c_int), ("orient", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("orient", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("max_cluster", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_slots", ctypes.c_int), ("device", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("max_cluster", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -186,7 +187,7 @@ def _stream(stream):
 
 
 def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, device=0, max_wait_spins=0,
-              kernel=0, factor=0, stencil=0, orient=0, boundary=0):
+              kernel=0, factor=0, stencil=0, orient=0, boundary=0, max_cluster=0):
     o = Opts()
     lib().ilu_opts_default(ctypes.byref(o))
     if deg is not None:
@@ -200,6 +201,7 @@ def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, d
     o.stencil = int(stencil)
     o.orient = int(orient)
     o.boundary = int(boundary)
+    o.max_cluster = int(max_cluster)
     return o
 
 
@@ -424,8 +426,8 @@ class Server:
     wait for their results; the loop admits them by free device memory and
     runs admitted solves concurrently."""
 
-    def __init__(self, budget_bytes=0.0, max_slots=0, device=0, precision=MIXED):
-        o = ServerOpts(float(budget_bytes), int(max_slots), int(device), int(precision))
+    def __init__(self, budget_bytes=0.0, max_slots=0, device=0, precision=MIXED, max_cluster=0):
+        o = ServerOpts(float(budget_bytes), int(max_slots), int(device), int(precision), int(max_cluster))
         h = ctypes.c_void_p()
         _check(lib().ilu_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.h = h

@@ -60,6 +60,7 @@ struct ilu_tet_s {
   bool use_band = false;
   int requested_slabs = 0, kernel_choice = ILU_KERNEL_AUTO, stencil_choice = ILU_STENCIL_AUTO;
   int perm[4] = {0, 1, 2, 3};  // vertex order used (ILU_ORIENT_LFA)
+  int max_cluster = 0;         // cap on CTAs per cluster (0: none)
   void *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa; float in F32)
   void *d_bnd = nullptr;       // boundary variant V1: exact factor records (sweep precision)
   int *d_bnd_off = nullptr;    // and their row offsets
@@ -183,7 +184,11 @@ ilu_status choose_clusters(ilu_tet t) {
   int qf[1 + kClusterCands] = {}, qb[1 + kClusterCands] = {};
   CK(launch_forward(L, nullptr, 0, nullptr, qf), "cluster query");
   CK(launch_backward(L, nullptr, 0, nullptr, qb), "cluster query");
-  const int cf = qf[0], cb = qb[0];
+  int cf = qf[0], cb = qb[0];
+  if (t->max_cluster > 0) {
+    cf = std::max(1, std::min(cf, t->max_cluster));
+    cb = std::max(1, std::min(cb, t->max_cluster));
+  }
   // as few clusters as the limit allows, as evenly filled as possible
   d.fwd.csize = (d.fwd.P + (d.fwd.P + cf - 1) / cf - 1) / ((d.fwd.P + cf - 1) / cf);
   d.bwd.csize = (d.bwd.P + (d.bwd.P + cb - 1) / cb - 1) / ((d.bwd.P + cb - 1) / cb);
@@ -639,6 +644,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->stencil = ILU_STENCIL_AUTO;
   o->orient = ILU_ORIENT_GIVEN;
   o->boundary = ILU_BOUNDARY_V2;
+  o->max_cluster = 0;
   return ILU_OK;
 }
 
@@ -724,6 +730,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
     t->requested_slabs = o.slabs;
     t->kernel_choice = o.kernel;
     t->stencil_choice = o.stencil;
+    t->max_cluster = o.max_cluster;
     st = upload(t);
     if (st != ILU_OK) {
       free_device(t);

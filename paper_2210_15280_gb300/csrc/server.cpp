@@ -318,6 +318,7 @@ void ilu_server_s::slot_main() {
       o.device = opts.device;
       o.orient = j.req.orient;
       o.boundary = j.req.boundary;
+      o.max_cluster = opts.max_cluster;
       if (j.key.mg)
         s = ilu_mg_setup(j.req.macro_tet, j.req.level, &j.req.coeff, j.req.poly_degree, 3, &o, &t.m);
       else

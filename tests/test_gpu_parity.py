@@ -269,3 +269,46 @@ def test_v1_boundary_variant_matches_oracle(g, orc, level, kind, prec):
     if level >= 5:
         x2 = orc.smooth(pr.A, pr.N, Ls, Dinv, x0.copy(), b, 2)
         assert rel(x2, xo) > 1e-9
+
+
+def test_bench_configuration_matches_oracle(g, orc):
+    """The default bench line's configuration exactly: the perturbed tet of
+    seed 3, level 7, kappa = 1 + 0.5 sin sin sin, degree 6, MIXED, automatic
+    kernel and stencil choices (slab kernels, stored stencils), b of seed 4,
+    x0 = 0; two sweeps against the oracle."""
+    level, deg = 7, 6
+    P = si.macro_tet(3)
+    co = ("sinprod", 1.0, 0.5, 0)
+    pr = orc.Problem(P, level, orc.Coeff(*co), deg=deg)
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=g.MIXED)
+    t.import_surrogate(pr.coefs)
+    b = si.rhs(level, 4)
+    x = np.zeros(si.num_nodes(level))
+    Ls, Dinv = pr.surrogate_factors()
+    xo = orc.smooth(pr.A, pr.N, Ls, Dinv, x.copy(), b, 2)
+    xd = dev(x, torch.float64)
+    t.smooth(xd, dev(b, torch.float64), 2)
+    assert rel(xd.cpu().numpy(), xo) < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["F64", "F32"])
+def test_exact_solution_is_a_fixed_point_at_level_9(g, prec):
+    """At the level-9 size of the bench (where the oracle is too slow for a
+    whole sweep): with b = A x* the sweep leaves x* in place, a property of
+    x <- x + C~^-1 (b - A x) at any size (F64 slab kernels, F32 band kernels)."""
+    level = 9
+    p = getattr(g, prec)
+    dt = torch.float32 if p == g.F32 else torch.float64
+    t = g.Tet(si.macro_tet(5), level, coeff=g.make_coeff("const"), poly_degree=6, precision=p)
+    xs = dev(si.interior_error(level, 7), dt)
+    r = torch.zeros_like(xs)
+    t.residual(xs, torch.zeros_like(xs), r)  # r = -A x* on the interior
+    b = -r
+    x = xs.clone()
+    t.smooth(x, b, 1)
+    d = (x - xs).abs().max().item() / xs.abs().max().item()
+    assert d < (1e-12 if p == g.F64 else 1e-4), d
+    # and from x = 0 the sweep moves towards x*
+    x0 = torch.zeros_like(xs)
+    t.smooth(x0, b, 2)
+    assert (x0 - xs).norm().item() < (xs).norm().item()

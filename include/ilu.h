@@ -86,6 +86,7 @@ typedef struct {
   int max_cluster;     /* at most this many CTAs per cluster in the slab kernels; <=0: the largest the
                         * device schedules (lowest latency for one tet; smaller clusters pack more
                         * concurrent tets onto the GPU) */
+  int values;          /* where FP64 substitutions take the surrogate values: an ilu_values_mode value */
 } ilu_opts;
 
 /* The two boundary variants of Sec. 4.1 and Alg. 2:
@@ -127,6 +128,27 @@ typedef enum { ILU_ORIENT_GIVEN = 0, ILU_ORIENT_LFA = 1 } ilu_orient;
  * sweeps store the coefficients in FP32 (14 x 4 bytes per point) and apply
  * them in FP32, the precision of their residual. */
 typedef enum { ILU_STENCIL_AUTO = 0, ILU_STENCIL_ON_THE_FLY = 1, ILU_STENCIL_STORED = 2 } ilu_stencil_mode;
+
+/* Where the FP64 substitutions take the surrogate values L~^p_d and
+ * 1/D~^p (Alg. 2 evaluates the polynomials at every point):
+ *   ILU_VALUES_ON_THE_FLY  evaluate the row polynomials at every point inside
+ *                          the substitutions (no storage beyond the row
+ *                          tables);
+ *   ILU_VALUES_TABULATED   evaluate them once for every grid point at set-up
+ *                          (again after ilu_import_surrogate), on the device
+ *                          with the same FP64 steps, and read them in the
+ *                          substitutions: 2 x 64 bytes per grid point.
+ *                          Levels <= 9;
+ *   ILU_VALUES_AUTO        tabulated for F64 handles up to level 9 (the two
+ *                          tables then take at most 2.9 GB); otherwise on
+ *                          the fly.
+ * The two give bit-identical sweeps.  The table trades memory for FP64
+ * arithmetic: the substitutions are a chain of dependent hyperplane steps,
+ * and on a GPU whose FP64 rate is a small fraction of its FP32 rate the
+ * per-point polynomial evaluation dominates each step.  FP32 and MIXED
+ * sweeps evaluate their FP32 polynomials on the fly (packed FP32 FMAs);
+ * ILU_VALUES_TABULATED with them is ILU_EINVAL. */
+typedef enum { ILU_VALUES_AUTO = 0, ILU_VALUES_ON_THE_FLY = 1, ILU_VALUES_TABULATED = 2 } ilu_values_mode;
 
 /* Which L D L^T preconditioner the surrogates approximate (Sec. 4.2):
  *   ILU_FACTOR_ILU0  exact ILU(0) of the interior block, by Alg. 1 (default);

@@ -23,6 +23,7 @@ RICHARDSON, PCG, MG_VCYCLE, MG_PCG = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND = 0, 1, 2
 FACTOR_ILU0, FACTOR_SGS = 0, 1
 STENCIL_AUTO, STENCIL_ON_THE_FLY, STENCIL_STORED = 0, 1, 2
+VALUES_AUTO, VALUES_ON_THE_FLY, VALUES_TABULATED = 0, 1, 2
 ORIENT_GIVEN, ORIENT_LFA = 0, 1
 BOUNDARY_V2, BOUNDARY_V1 = 0, 1
 STATUS_NAMES = ["ILU_OK", "ILU_EINVAL", "ILU_ENOMEM", "ILU_ECUDA", "ILU_ESINGULAR", "ILU_ENOTCONV",
@@ -56,7 +57,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("slabs", ctypes.c_int), ("device", ctypes.c_int),
                 ("max_wait_spins", ctypes.c_longlong), ("kernel", ctypes.c_int), ("factor", ctypes.c_int),
                 ("stencil", ctypes.c_int), ("orient", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("max_cluster", ctypes.c_int)]
+                ("max_cluster", ctypes.c_int), ("values", ctypes.c_int)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -187,7 +188,7 @@ def _stream(stream):
 
 
 def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, device=0, max_wait_spins=0,
-              kernel=0, factor=0, stencil=0, orient=0, boundary=0, max_cluster=0):
+              kernel=0, factor=0, stencil=0, orient=0, boundary=0, max_cluster=0, values=0):
     o = Opts()
     lib().ilu_opts_default(ctypes.byref(o))
     if deg is not None:
@@ -202,6 +203,7 @@ def make_opts(deg=None, sample_level=-1, ridge=-1.0, precision=MIXED, slabs=0, d
     o.orient = int(orient)
     o.boundary = int(boundary)
     o.max_cluster = int(max_cluster)
+    o.values = int(values)
     return o
 
 

@@ -132,12 +132,13 @@ void release(ilu_batch b) {
 // between clusters), else the size with the most resident CTAs.
 ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   const int n = b->n;
-  // groups keyed by (level, register degree class, padded row length)
+  // groups keyed by (level, polynomial class, padded row length); classes:
+  // rows in registers, rows in shared memory, tabulated values
+  auto cls = [](const TetView &v) { return v.reg >= 0 ? 1 : (v.reg == kWaveTabulated ? 2 : 0); };
   std::map<std::tuple<int, int, int>, int> key;
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
-    const bool reg = wave_uses_registers(v.kind, v.dx);
-    const auto k = std::make_tuple(-v.N, reg ? 1 : 0, v.rstride);  // largest levels first
+    const auto k = std::make_tuple(-v.N, cls(v), v.rstride);  // largest levels first
     auto it = key.find(k);
     if (it == key.end()) {
       it = key.emplace(k, 0).first;
@@ -149,11 +150,10 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   b->groups.assign(key.size(), Group{});
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
-    const bool reg = wave_uses_registers(v.kind, v.dx);
-    Group &g = b->groups[key[std::make_tuple(-v.N, reg ? 1 : 0, v.rstride)]];
+    Group &g = b->groups[key[std::make_tuple(-v.N, cls(v), v.rstride)]];
     g.N = v.N;
     g.dxp = v.rstride;
-    g.reg = reg ? std::max(g.reg, v.dx) : -1;
+    g.reg = v.reg >= 0 ? std::max(g.reg, v.reg) : v.reg;
     g.members.push_back(i);
   }
   // per-tet descriptors with geometry and progress words in the batch's flag array
@@ -165,8 +165,8 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       DevTet d = *v.dev;
       const int layers = std::max(1, v.N - 3);
       const int requested = b->explicit_slabs > 0 ? b->explicit_slabs : (zb_pref > 0 ? (layers + zb_pref - 1) / zb_pref : 0);
-      d.fwd = wave_geom(v.N, v.kind, v.rstride, v.dx, true, requested);
-      d.bwd = wave_geom(v.N, v.kind, v.rstride, v.dx, false, requested);
+      d.fwd = wave_geom(v.N, v.kind, v.rstride, v.reg, true, requested);
+      d.bwd = wave_geom(v.N, v.kind, v.rstride, v.reg, false, requested);
       d.fwd.prog = off;
       d.bwd.prog = off + d.fwd.P;
       off += d.fwd.P + d.bwd.P;
@@ -211,8 +211,8 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       L.v1 = L.v1 || d.bnd != nullptr;
       L.block_f = std::max(L.block_f, (d.fwd.zb * d.fwd.wpl + 1) * 32);
       L.block_b = std::max(L.block_b, (d.bwd.zb * d.bwd.wpl + 1) * 32);
-      L.smem_f = std::max(L.smem_f, wave_smem_bytes(v.N, d.fwd, b->kind, v.rstride, G.reg < 0 ? 99 : G.reg, true));
-      L.smem_b = std::max(L.smem_b, wave_smem_bytes(v.N, d.bwd, b->kind, v.rstride, G.reg < 0 ? 99 : G.reg, false));
+      L.smem_f = std::max(L.smem_f, wave_smem_bytes(v.N, d.fwd, b->kind, v.rstride, G.reg, true));
+      L.smem_b = std::max(L.smem_b, wave_smem_bytes(v.N, d.bwd, b->kind, v.rstride, G.reg, false));
       L.maxP_f = std::max(L.maxP_f, d.fwd.P);
       L.maxP_b = std::max(L.maxP_b, d.bwd.P);
     }

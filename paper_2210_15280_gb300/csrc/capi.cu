@@ -64,6 +64,8 @@ struct ilu_tet_s {
   void *d_astore = nullptr;  // stored off-diagonal coefficients, 14 planes of nnodes (variable kappa; float in F32)
   void *d_bnd = nullptr;       // boundary variant V1: exact factor records (sweep precision)
   int *d_bnd_off = nullptr;    // and their row offsets
+  bool tabulate = false;       // FP64 substitutions read tabulated surrogate values
+  double *d_valsF = nullptr, *d_valsB = nullptr;  // those tables (8 doubles per grid point each)
   int band_Z = 8, band_ntiles = 0, band_ncta = 0;
   BandInfo *d_binfo = nullptr;
   int *d_bint = nullptr;  // CTA list, tile list, cluster map {0, ncta, 0}, tile prefix {0, ntiles}, epoch
@@ -92,6 +94,11 @@ struct ilu_tet_s {
   std::mutex mu;
   size_t elem() const { return precision == ILU_F32 ? sizeof(float) : sizeof(double); }
   int kind() const { return precision == ILU_F64 ? kSweepF64 : (precision == ILU_F32 ? kSweepF32 : kSweepMixed); }
+  // WaveLaunch.reg code of the slab substitutions
+  int wave_reg() const {
+    if (tabulate) return kWaveTabulated;
+    return wave_uses_registers(kind(), host.dx) ? host.dx : -1;
+  }
   size_t nnodes() const { return (size_t)grid_nodes(host.N); }
 };
 
@@ -106,6 +113,8 @@ void free_device(ilu_tet t) {
   t->ev_pool.clear();
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa); cudaFree(t->d_astore);
   cudaFree(t->d_bnd); cudaFree(t->d_bnd_off);
+  cudaFree(t->d_valsF); cudaFree(t->d_valsB);
+  t->d_valsF = t->d_valsB = nullptr;
   t->d_astore = nullptr;
   t->d_bnd = nullptr;
   t->d_bnd_off = nullptr;
@@ -132,17 +141,17 @@ void free_device(ilu_tet t) {
 // Thin slabs are the default: inside a cluster a hop between slabs costs a
 // few hundred cycles, while every extra layer adds its warps' issue time to
 // each level of the slab.
-WaveGeom pick_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
+WaveGeom pick_geom(int N, int kind, int dxp, int reg, bool fwd, int requested) {
   const int layers = std::max(1, N - 3);
   WaveGeom g = {};
   g.wpl = std::max(1, std::min(8, (N / 2 + 31) / 32));
-  const int max_warps = wave_uses_registers(kind, dx) ? 15 : 31;  // plus the communication warp
+  const int max_warps = reg >= 0 ? 15 : 31;  // plus the communication warp
   int zb = std::max(1, max_warps / g.wpl);
   zb = std::min(zb, requested > 0 ? (layers + requested - 1) / requested : 2);
   zb = std::min(zb, layers);
   while (zb > 1) {
     g.zb = zb;
-    if (wave_smem_bytes(N, g, kind, dxp, dx, fwd) <= 200 * 1024) break;
+    if (wave_smem_bytes(N, g, kind, dxp, reg, fwd) <= 200 * 1024) break;
     --zb;
   }
   g.zb = zb;
@@ -153,8 +162,8 @@ WaveGeom pick_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
 void choose_geometry(ilu_tet t, int requested) {
   const int N = t->host.N;
   DevTet &d = t->dev;
-  d.fwd = pick_geom(N, t->kind(), t->host.rstride, t->host.dx, true, requested);
-  d.bwd = pick_geom(N, t->kind(), t->host.rstride, t->host.dx, false, requested);
+  d.fwd = pick_geom(N, t->kind(), t->host.rstride, t->wave_reg(), true, requested);
+  d.bwd = pick_geom(N, t->kind(), t->host.rstride, t->wave_reg(), false, requested);
   d.fwd.prog = 0;
   d.bwd.prog = d.fwd.P;
   d.fwd.ticket = d.fwd.P + d.bwd.P;
@@ -172,13 +181,13 @@ ilu_status choose_clusters(ilu_tet t) {
   L = {};
   L.tets = t->d_dev;
   L.kind = t->kind();
-  L.reg = wave_uses_registers(L.kind, h.dx) ? h.dx : -1;
+  L.reg = t->wave_reg();
   L.dxp = h.rstride;
   L.v1 = h.boundary == ILU_BOUNDARY_V1;
   L.block_f = (d.fwd.zb * d.fwd.wpl + 1) * 32;
   L.block_b = (d.bwd.zb * d.bwd.wpl + 1) * 32;
-  L.smem_f = wave_smem_bytes(h.N, d.fwd, L.kind, h.rstride, h.dx, true);
-  L.smem_b = wave_smem_bytes(h.N, d.bwd, L.kind, h.rstride, h.dx, false);
+  L.smem_f = wave_smem_bytes(h.N, d.fwd, L.kind, h.rstride, L.reg, true);
+  L.smem_b = wave_smem_bytes(h.N, d.bwd, L.kind, h.rstride, L.reg, false);
   L.maxP_f = d.fwd.P;
   L.maxP_b = d.bwd.P;
   int qf[1 + kClusterCands] = {}, qb[1 + kClusterCands] = {};
@@ -373,6 +382,18 @@ ilu_status upload(ilu_tet t) {
       d.astore = t->d_astore;
     }
   }
+  d.valsF = d.valsB = nullptr;
+  if (t->tabulate) {
+    const size_t vbytes = nn * 8 * sizeof(double);
+    CK(cudaMalloc(&t->d_valsF, vbytes), "cudaMalloc tabulated values");
+    CK(cudaMalloc(&t->d_valsB, vbytes), "cudaMalloc tabulated values");
+    CK(cudaMemset(t->d_valsF, 0, vbytes), "cudaMemset tabulated values");
+    CK(cudaMemset(t->d_valsB, 0, vbytes), "cudaMemset tabulated values");
+    CK(launch_tabulate(d, t->d_valsF, t->d_valsB, cudaStreamPerThread), "tabulation launch");
+    CK(cudaStreamSynchronize(cudaStreamPerThread), "tabulation");
+    d.valsF = t->d_valsF;
+    d.valsB = t->d_valsB;
+  }
   return choose_clusters(t);
 }
 
@@ -388,6 +409,10 @@ ilu_status upload_tables(ilu_tet t) {
   if (nb)
     CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(), nb * es,
                   cudaMemcpyHostToDevice), "upload tables");
+  if (t->tabulate) {  // the tabulated values follow the new polynomials
+    CK(launch_tabulate(t->dev, t->d_valsF, t->d_valsB, cudaStreamPerThread), "tabulation launch");
+    CK(cudaStreamSynchronize(cudaStreamPerThread), "tabulation");
+  }
   return ILU_OK;
 }
 
@@ -596,12 +621,13 @@ bool tet_view(ilu_tet t, TetView *v) {
   v->device = t->device;
   v->precision = t->precision;
   v->kind = t->kind();
+  v->reg = t->wave_reg();
   v->nnodes = t->nnodes();
   v->failed = t->failed;
   return true;
 }
-WaveGeom wave_geom(int N, int kind, int dxp, int dx, bool fwd, int requested) {
-  return pick_geom(N, kind, dxp, dx, fwd, requested);
+WaveGeom wave_geom(int N, int kind, int dxp, int reg, bool fwd, int requested) {
+  return pick_geom(N, kind, dxp, reg, fwd, requested);
 }
 ilu_status tet_sweeps(ilu_tet t, void *x, const void *b, int n, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(t->mu);
@@ -645,6 +671,7 @@ ilu_status ilu_opts_default(ilu_opts *o) {
   o->orient = ILU_ORIENT_GIVEN;
   o->boundary = ILU_BOUNDARY_V2;
   o->max_cluster = 0;
+  o->values = ILU_VALUES_AUTO;
   return ILU_OK;
 }
 
@@ -684,6 +711,11 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (o.boundary != ILU_BOUNDARY_V2 && o.boundary != ILU_BOUNDARY_V1) return fail(ILU_EINVAL, "unknown boundary variant");
   if (o.boundary == ILU_BOUNDARY_V1 && o.kernel == ILU_KERNEL_BAND)
     return fail(ILU_EINVAL, "boundary variant V1 runs on the slab kernels");
+  if (o.values < ILU_VALUES_AUTO || o.values > ILU_VALUES_TABULATED) return fail(ILU_EINVAL, "unknown values choice");
+  if (o.values == ILU_VALUES_TABULATED && o.precision != ILU_F64)
+    return fail(ILU_EINVAL, "tabulated surrogate values are an FP64 option");
+  if (o.values == ILU_VALUES_TABULATED && level > kTabulatedMaxLevel)
+    return fail(ILU_EINVAL, "tabulated surrogate values need level <= 9");
   int perm[4] = {0, 1, 2, 3};
   if (o.orient == ILU_ORIENT_LFA) {
     ilu_status ls = ilu_lfa_order(macro_tet, perm, nullptr, nullptr);
@@ -725,6 +757,11 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
       cudaGetLastError();
       delete t;
       return fail(ILU_ENODEV, "no CUDA device with that ordinal");
+    }
+    {
+      const size_t vbytes = 2 * (size_t)grid_nodes(1 << level) * 8 * sizeof(double);
+      t->tabulate = o.precision == ILU_F64 && level <= kTabulatedMaxLevel &&
+                    (o.values == ILU_VALUES_TABULATED || (o.values == ILU_VALUES_AUTO && vbytes <= ((size_t)4 << 30)));
     }
     choose_geometry(t, o.slabs);
     t->requested_slabs = o.slabs;

@@ -61,6 +61,9 @@ struct DevTet {
   int64_t astride;
   const void *bnd;       // boundary variant V1: 8 values per cell-boundary point (sweep precision), or null
   const int *bnd_off;    // its row offsets (bnd_record in grid.h)
+  const double *valsF;   // FP64 sweeps with tabulated surrogate values, 8 per grid point at 8 * index:
+  const double *valsB;   // forward L~^p_d (d in D_l) and 0; backward 1/D~^p, L~^{p-d}_d.  Null: the
+                         // substitutions evaluate the row polynomials themselves
 };
 
 struct LaunchStatus {
@@ -106,7 +109,8 @@ struct BatchMap {
 struct WaveLaunch {
   const DevTet *tets;  // device array
   int kind;            // SweepKind
-  int reg;             // register path: row degree (0..7), or -1 (rows read from shared memory)
+  int reg;             // register path: row degree (0..7); -1: rows read from shared memory;
+                       // kWaveTabulated: surrogate values read from the tet's tables
   int dxp;             // padded coefficients per row function (rstride of the tets)
   BatchMap map_f, map_b;
   int block_f, block_b;    // threads per CTA
@@ -128,10 +132,18 @@ cudaError_t launch_forward(const WaveLaunch &L, LaunchStatus *status, long long 
                            int *cluster_query = nullptr);
 cudaError_t launch_backward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
                             int *cluster_query = nullptr);
-size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool forward);
+// reg: the WaveLaunch.reg code of the launch
+size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int reg, bool forward);
 // FP32/MIXED sweeps of degree <= 7 keep each row's polynomials in registers
 // (CTAs of at most 16 warps); otherwise they are read from shared memory.
 bool wave_uses_registers(int kind, int dx);
+// WaveLaunch.reg value of FP64 sweeps that read tabulated surrogate values
+constexpr int kWaveTabulated = -2;
+// Highest level whose tabulated-value staging fits a CTA's shared memory.
+constexpr int kTabulatedMaxLevel = 9;
+// Fill valsF / valsB (8 doubles per grid point each) from the FP64 row
+// tables of t, with the arithmetic of the substitutions' own evaluation.
+cudaError_t launch_tabulate(const DevTet &t, double *valsF, double *valsB, cudaStream_t st);
 int residual_blocks(int N);  // blocks of the residual launch (8 row chunks each)
 int rowgrid_blocks(int N);   // blocks of the row-per-warp reductions (interior norm)
 int residual_chunks(int N);
@@ -168,12 +180,13 @@ cudaError_t launch_band_update(int kind, const DevTet *tets, const int *tprefix,
 struct TetView {
   const DevTet *dev;  // host copy of the device descriptor
   int N, dx, rstride, device, precision, kind;
+  int reg;  // WaveLaunch.reg code of its substitutions
   size_t nnodes;
   bool failed;
 };
 bool tet_view(ilu_tet_s *t, TetView *v);
 // partition of one substitution (requested > 0: about that many slabs)
-WaveGeom wave_geom(int N, int kind, int dxp, int dx, bool fwd, int requested);
+WaveGeom wave_geom(int N, int kind, int dxp, int reg, bool fwd, int requested);
 
 // solver helpers on full-grid vectors (double if f64, else float)
 constexpr int kDotPartials = 512;

@@ -127,6 +127,7 @@ size_t estimate_tet_bytes(int level, int precision, int degree, bool var) {
   b += nn * ew;                         // scratch w
   if (var) b += nn * 8;                 // kappa
   if (var && 14 * nn * 8 <= ((size_t)4 << 30)) b += 14 * nn * 8;  // stored stencils (ILU_STENCIL_AUTO)
+  if (precision == ILU_F64 && level <= 9) b += 16 * nn * 8;  // tabulated surrogate values (ILU_VALUES_AUTO)
   b += 5 * nn * ex;                     // Krylov vectors
   b += (N * N / 8 + 4096) * 8;          // partial sums, flags, norms
   return b + (1u << 20);                // allocation granularity

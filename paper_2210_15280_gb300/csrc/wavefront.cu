@@ -16,7 +16,9 @@
 //          result and x in the backward pass), filled by cp.async D levels
 //          ahead,
 //   coef   the polynomials of every active row, filled by cp.async D levels
-//          before the row's first point.
+//          before the row's first point; in FP64 sweeps with tabulated
+//          surrogate values, the 8 values of each point of the next levels
+//          instead (filled with the inputs).
 // Neighbouring slabs.  The slabs of a tet are launched as thread-block
 // clusters.  Inside a cluster the warps of a slab's boundary layer write
 // their results straight into the neighbour CTA's halo ring (distributed
@@ -130,6 +132,22 @@ __device__ __forceinline__ void eval_rows(const T *c, T t, T (&out)[NF]) {
 #pragma unroll
     for (int k = DXP - 2; k >= 0; --k) v = fma(v, t, a[f * DXP + k]);
     out[f] = v;
+  }
+}
+
+// the 8 tabulated values of one point from shared memory (16-byte loads)
+template <typename T>
+__device__ __forceinline__ void load_values(const T *v, T (&out)[8]) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double2 q = reinterpret_cast<const double2 *>(v)[i];
+      out[2 * i] = q.x;
+      out[2 * i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) out[i] = v[i];
   }
 }
 
@@ -418,6 +436,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
                                                                    LaunchStatus *status, long long max_spins) {
   constexpr int NF = 7;
   constexpr bool F32 = sizeof(TW) == 4;
+  constexpr bool TAB = REG == kWaveTabulated;    // values read from t.valsF
   constexpr int ROW = F32 ? 8 * DXP : NF * DXP;  // elements per cached row
   const int NCW = (int)(blockDim.x >> 5) - 1, NCT = NCW * 32;  // compute warps (+ one communication warp)
   __shared__ int s_ticket, s_abort, s_nb, s_done, s_cdone;
@@ -445,7 +464,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
   TW *ring = reinterpret_cast<TW *>(smem);          // [4][Zb][RC]  w of the last levels
   TW *rin = ring + 4 * Zb * RC;                     // [IS][Zb][RC] r of the next levels
   TW *halo = rin + IS * Zb * RC;                    // [HS][RC]     layer z_s - 1
-  TW *coef = align16<TW>(halo + HS * RC);           // [Zb][RCC][ROW]
+  TW *coef = align16<TW>(halo + HS * RC);           // [Zb][RCC][ROW], tabulated: [IS][Zb][RC][8]
   const int k = (s_ticket - bm.prefix[owner]) * (int)C + (int)rank;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k < P) {
@@ -485,11 +504,19 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
         constexpr int CH = ROW * (int)sizeof(TW) / 16;
         for (int c = lane; c < CH; c += 32) cp_async<16>(dst + 16 * c, src + 16 * c);
       };
-      auto fetch_in = [&](int s2) {  // r of this warp's points on level s2
+      auto fetch_in = [&](int s2) {  // r (and tabulated values) of this warp's points on level s2
         const int ylo = ylo_of(N, s2, z), yhi = yhi_of(N, s2, z);
-        TW *dst = rin + (size_t)(s2 & (IS - 1)) * SS + li * RC;
-        for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl)
-          cp_async<(int)sizeof(TW)>(dst + (y - ylo), wg + ix.at(s2 - 2 * y - 3 * z, y));
+        const size_t at = (size_t)(s2 & (IS - 1)) * SS + li * RC;
+        for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl) {
+          const int gi = ix.at(s2 - 2 * y - 3 * z, y);
+          cp_async<(int)sizeof(TW)>(rin + at + (y - ylo), wg + gi);
+          if constexpr (TAB) {
+            const char *src = reinterpret_cast<const char *>(t.valsF + (size_t)gi * 8);
+            char *dst = reinterpret_cast<char *>(coef + (at + (y - ylo)) * 8);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp_async<16>(dst + 16 * c, src + 16 * c);
+          }
+        }
       };
 
       // register path: the row this lane owns (rows y with (y-1) mod 32*wpl == 32*sub + lane)
@@ -498,7 +525,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
       RowRegs<(REG >= 0 ? REG : 0)> regs;
       if (active) {
         for (int s2 = s_begin; s2 < s_begin + D; ++s2) {
-          if (sub == 0) fetch_row(s2);
+          if (!TAB && sub == 0) fetch_row(s2);
           fetch_in(s2);
         }
       }
@@ -507,7 +534,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
       bool stop = sync_or(NCT, false);
       for (int s = s_begin; s <= s_end && !stop; ++s) {
         if (active) {
-          if (sub == 0) fetch_row(s + D);
+          if (!TAB && sub == 0) fetch_row(s + D);
           fetch_in(s + D);
         }
         cp_commit();
@@ -628,6 +655,13 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) fwd_wave(const DevTet *
               regs.eval((TW)(2 * x - (N - ycur - z)) * hh, L);
               point(ycur, L);
             }
+          } else if constexpr (TAB) {
+            const TW *vv = coef + ((size_t)(s & (IS - 1)) * SS + li * RC) * 8;
+            for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl) {
+              TW L[8];
+              load_values(vv + (size_t)(y - ylo) * 8, L);
+              point(y, L);
+            }
           } else {
             int slot = ylo % RCC + 32 * sub + lane;
             for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl, slot += 32 * wpl) {
@@ -666,6 +700,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
                                                                    LaunchStatus *status, long long max_spins) {
   constexpr int NF = 8;
   constexpr bool F32 = sizeof(TW) == 4;
+  constexpr bool TAB = REG == kWaveTabulated;  // values read from t.valsB
   constexpr int ROW = NF * DXP;  // elements per cached row (FP32: 4 pairs x DXP x 2)
   const int NCW = (int)(blockDim.x >> 5) - 1, NCT = NCW * 32;
   __shared__ int s_ticket, s_abort, s_nb, s_done, s_cdone;
@@ -697,7 +732,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
   TW *win = ring + 4 * Zb * RC;                  // [IS][Zb][RC] forward result of the next levels
   TW *halo = win + IS * Zb * RC;                 // [HS][RC]     layer z_e
   TX *xin = align16<TX>(halo + HS * RC);         // [IS][Zb][RC] x of the next levels
-  TW *coef = align16<TW>(xin + IS * Zb * RC);    // [Zb][RCC][ROW]
+  TW *coef = align16<TW>(xin + IS * Zb * RC);    // [Zb][RCC][ROW], tabulated: [IS][Zb][RC][8]
   const int Q = bm.prefix[owner + 1] - bm.prefix[owner];  // clusters of this tet
   const int k = (Q - 1 - (s_ticket - bm.prefix[owner])) * (int)C + (int)rank;  // top clusters first
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -737,14 +772,19 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
         constexpr int CH = ROW * (int)sizeof(TW) / 16;
         for (int c = lane; c < CH; c += 32) cp_async<16>(dst + 16 * c, src + 16 * c);
       };
-      auto fetch_in = [&](int s2) {  // forward result and x of this warp's points on level s2
+      auto fetch_in = [&](int s2) {  // forward result, x (and tabulated values) of this warp's points on level s2
         const int ylo = ylo_of(N, s2, z), yhi = yhi_of(N, s2, z);
-        TW *dw = win + (size_t)(s2 & (IS - 1)) * SS + li * RC;
-        TX *dx = xin + (size_t)(s2 & (IS - 1)) * SS + li * RC;
+        const size_t at = (size_t)(s2 & (IS - 1)) * SS + li * RC;
         for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl) {
           const int gi = ix.at(s2 - 2 * y - 3 * z, y);
-          cp_async<(int)sizeof(TW)>(dw + (y - ylo), wg + gi);
-          cp_async<(int)sizeof(TX)>(dx + (y - ylo), xg + gi);
+          cp_async<(int)sizeof(TW)>(win + at + (y - ylo), wg + gi);
+          cp_async<(int)sizeof(TX)>(xin + at + (y - ylo), xg + gi);
+          if constexpr (TAB) {
+            const char *src = reinterpret_cast<const char *>(t.valsB + (size_t)gi * 8);
+            char *dst = reinterpret_cast<char *>(coef + (at + (y - ylo)) * 8);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp_async<16>(dst + 16 * c, src + 16 * c);
+          }
         }
       };
 
@@ -755,7 +795,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
       RowRegs<(REG >= 0 ? REG : 0)> regs;
       if (active) {
         for (int s2 = s_end; s2 > s_end - D; --s2) {
-          if (sub == 0) fetch_row(s2);
+          if (!TAB && sub == 0) fetch_row(s2);
           fetch_in(s2);
         }
       }
@@ -764,7 +804,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
       bool stop = sync_or(NCT, false);
       for (int s = s_end; s >= s_begin && !stop; --s) {
         if (active) {
-          if (sub == 0) fetch_row(s - D);
+          if (!TAB && sub == 0) fetch_row(s - D);
           fetch_in(s - D);
         }
         cp_commit();
@@ -879,6 +919,13 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
               regs.eval((TW)(2 * x - (N - ycur - z)) * hh, L);
               point(ycur, L);
             }
+          } else if constexpr (TAB) {
+            const TW *vv = coef + ((size_t)(s & (IS - 1)) * SS + li * RC) * 8;
+            for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl) {
+              TW L[8];
+              load_values(vv + (size_t)(y - ylo) * 8, L);
+              point(y, L);
+            }
           } else {
             int slot = ylo % RCC + 32 * sub + lane;
             for (int y = ylo + 32 * sub + lane; y <= yhi; y += 32 * wpl, slot += 32 * wpl) {
@@ -906,17 +953,25 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
   cl_sync();
 }
 
+// coefficient area: row polynomials (register ring or row cache), or the
+// tabulated values of the next IS levels
 template <typename TW>
-size_t fwd_smem(int N, const WaveGeom &g, int dxp, bool reg) {
-  const size_t RC = level_cap(N), RCC = reg ? kRowRing : cache_rows(N);
-  const size_t nf = sizeof(TW) == 4 ? 8 : 7;
-  return sizeof(TW) * ((4 + IS) * g.zb * RC + HS * RC) + 16 + (size_t)g.zb * RCC * nf * dxp * sizeof(TW);
+size_t coef_smem(int N, const WaveGeom &g, int dxp, int reg, int nf) {
+  const size_t RC = level_cap(N);
+  if (reg == kWaveTabulated) return sizeof(TW) * IS * g.zb * RC * 8;
+  const size_t RCC = reg >= 0 ? kRowRing : cache_rows(N);
+  return (size_t)g.zb * RCC * nf * dxp * sizeof(TW);
+}
+template <typename TW>
+size_t fwd_smem(int N, const WaveGeom &g, int dxp, int reg) {
+  const size_t RC = level_cap(N);
+  return sizeof(TW) * ((4 + IS) * g.zb * RC + HS * RC) + 16 + coef_smem<TW>(N, g, dxp, reg, sizeof(TW) == 4 ? 8 : 7);
 }
 template <typename TW, typename TX>
-size_t bwd_smem(int N, const WaveGeom &g, int dxp, bool reg) {
-  const size_t RC = level_cap(N), RCC = reg ? kRowRing : cache_rows(N);
+size_t bwd_smem(int N, const WaveGeom &g, int dxp, int reg) {
+  const size_t RC = level_cap(N);
   return sizeof(TW) * ((4 + IS) * g.zb * RC + HS * RC) + 16 + sizeof(TX) * IS * g.zb * RC + 16 +
-         (size_t)g.zb * RCC * 8 * dxp * sizeof(TW);
+         coef_smem<TW>(N, g, dxp, reg, 8);
 }
 
 // Launch as clusters of `csize` CTAs covering `clusters` clusters.  With
@@ -1023,12 +1078,56 @@ cudaError_t bwd32(const WaveLaunch &L, LaunchStatus *s, long long m, cudaStream_
   }
 }
 
+// Surrogate values of every interior point for FP64 sweeps that read them
+// from tables: one block per row (y, z), threads over x.  The values are the
+// ones the substitutions would evaluate themselves: the same row
+// polynomials, the same abscissa and the same Horner steps (eval_rows), so
+// the two ways give bit-identical sweeps.
+template <int DXP>
+__global__ void __launch_bounds__(128) tabulate_kernel(const DevTet t, double *__restrict__ valsF,
+                                                       double *__restrict__ valsB) {
+  const int N = t.N;
+  const int y = (int)blockIdx.x + 1, z = (int)blockIdx.y + 1;
+  if (y > N - 2 - z) return;
+  const LayerIx ix = layer_ix(N, z);
+  const size_t row = (size_t)row_id(N, y, z);
+  const double *cf = reinterpret_cast<const double *>(t.tabF) + row * 7 * DXP;
+  const double *cb = reinterpret_cast<const double *>(t.tabB) + row * 8 * DXP;
+  const double hh = (double)(0.5 * t.h);
+  for (int x = 1 + (int)threadIdx.x; x <= N - 1 - y - z; x += (int)blockDim.x) {
+    const double tt = (double)(2 * x - (N - y - z)) * hh;
+    double f[7], b[8];
+    eval_rows<double, DXP, 7>(cf, tt, f);
+    eval_rows<double, DXP, 8>(cb, tt, b);
+    const size_t gi = (size_t)ix.at(x, y);
+    double2 *of = reinterpret_cast<double2 *>(valsF + gi * 8);
+    double2 *ob = reinterpret_cast<double2 *>(valsB + gi * 8);
+    of[0] = make_double2(f[0], f[1]);
+    of[1] = make_double2(f[2], f[3]);
+    of[2] = make_double2(f[4], f[5]);
+    of[3] = make_double2(f[6], 0.0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ob[i] = make_double2(b[2 * i], b[2 * i + 1]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_tabulate(const DevTet &t, double *valsF, double *valsB, cudaStream_t st) {
+  if (t.N < 4) return cudaSuccess;
+  const dim3 grid(t.N - 3, t.N - 3);
+  switch (t.rstride) {
+    case 4: tabulate_kernel<4><<<grid, 128, 0, st>>>(t, valsF, valsB); break;
+    case 8: tabulate_kernel<8><<<grid, 128, 0, st>>>(t, valsF, valsB); break;
+    case 16: tabulate_kernel<16><<<grid, 128, 0, st>>>(t, valsF, valsB); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 bool wave_uses_registers(int kind, int dx) { return kind != kSweepF64 && dx <= 7; }
 
-size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool forward) {
-  const bool reg = wave_uses_registers(kind, dx);
+size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int reg, bool forward) {
   if (forward) return kind == kSweepF64 ? fwd_smem<double>(N, g, dxp, reg) : fwd_smem<float>(N, g, dxp, reg);
   if (kind == kSweepF64) return bwd_smem<double, double>(N, g, dxp, reg);
   if (kind == kSweepMixed) return bwd_smem<float, double>(N, g, dxp, reg);
@@ -1038,6 +1137,7 @@ size_t wave_smem_bytes(int N, const WaveGeom &g, int kind, int dxp, int dx, bool
 cudaError_t launch_forward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
                            int *cluster_query) {
   if (L.kind == kSweepF64) {
+    if (L.reg == kWaveTabulated) return fwd_launch<double, 4, kWaveTabulated>(L, status, max_spins, st, cluster_query);
     if (L.dxp == 4) return fwd_launch<double, 4, -1>(L, status, max_spins, st, cluster_query);
     if (L.dxp == 8) return fwd_launch<double, 8, -1>(L, status, max_spins, st, cluster_query);
     return fwd_launch<double, 16, -1>(L, status, max_spins, st, cluster_query);
@@ -1048,6 +1148,8 @@ cudaError_t launch_forward(const WaveLaunch &L, LaunchStatus *status, long long 
 cudaError_t launch_backward(const WaveLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st,
                             int *cluster_query) {
   if (L.kind == kSweepF64) {
+    if (L.reg == kWaveTabulated)
+      return bwd_launch<double, double, 4, kWaveTabulated>(L, status, max_spins, st, cluster_query);
     if (L.dxp == 4) return bwd_launch<double, double, 4, -1>(L, status, max_spins, st, cluster_query);
     if (L.dxp == 8) return bwd_launch<double, double, 8, -1>(L, status, max_spins, st, cluster_query);
     return bwd_launch<double, double, 16, -1>(L, status, max_spins, st, cluster_query);

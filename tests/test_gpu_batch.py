@@ -136,3 +136,27 @@ def test_batch_with_v1_tets_equals_single_sweeps(g):
     for i, (x, r) in enumerate(zip(xs, ref)):
         assert torch.equal(x, r), i
     batch.close()
+
+
+def test_f64_batch_mixing_tabulated_and_evaluated_tets(g):
+    """F64 tets whose substitutions read tabulated values and tets that
+    evaluate the polynomials run in separate groups of one batch; each gives
+    its single-tet sweep bit for bit."""
+    mesh = si.macro_mesh(12, n_tets=4)
+    spec = [(5, 4, g.VALUES_TABULATED), (5, 4, g.VALUES_ON_THE_FLY), (6, 6, g.VALUES_AUTO), (4, 2, g.VALUES_ON_THE_FLY)]
+    tets = []
+    for i, (P, (L, d, v)) in enumerate(zip(mesh, spec)):
+        co = COEFFS[i % 3]
+        tets.append((P, L, d, co, g.Tet(P, L, coeff=g.make_coeff(*co), poly_degree=d, precision=g.F64, values=v)))
+    xs, bs = vectors(tets, torch.float64, 500)
+    ref = [x.clone() for x in xs]
+    for (P, L, d, co, t), x, b in zip(tets, ref, bs):
+        t.smooth(x, b, 2)
+    torch.cuda.synchronize()
+    batch = g.Batch([t for *_, t in tets])
+    batch.smooth(xs, bs, 2)
+    for i, (x, r) in enumerate(zip(xs, ref)):
+        assert torch.equal(x, r), f"tet {i}"
+    batch.close()
+    for *_, t in tets:
+        t.close()

@@ -246,6 +246,37 @@ def test_stored_stencil_bitwise_equals_on_the_fly(g, orc, level, prec, kernel):
     assert rel(out[1][0].astype(np.float64), xo) < (1e-12 if p == g.F64 else 2e-5)
 
 
+@pytest.mark.parametrize("level,kind,deg,boundary,slabs", [
+    (2, "const", 2, "V2", 0), (4, "const", 2, "V2", 0), (5, "sinprod", 6, "V2", 0), (6, "kappa_i", 9, "V2", 0),
+    (5, "sinprod", 4, "V1", 0), (7, "sinprod", 6, "V2", 0), (7, "const", 3, "V2", 125), (6, "sinprod", 5, "V1", 7)])
+def test_tabulated_values_bitwise_equal_on_the_fly(g, level, kind, deg, boundary, slabs):
+    """ilu_opts.values: F64 substitutions that read the surrogate values from
+    the set-up tables give the sweep of those that evaluate the row
+    polynomials at every point, bit for bit (same FP64 Horner steps), for
+    every padded row length (degrees 2, 6, 9), both boundary variants and
+    several slab partitions; also after new coefficients are imported."""
+    co = {"const": ("const", 1.0, 0.0, 0), "sinprod": ("sinprod", 1.0, 0.5, 0),
+          "kappa_i": ("kappa_i", 0.0, 0.0, 2)}[kind]
+    P = si.macro_tet(80 + level)
+    bnd = g.BOUNDARY_V1 if boundary == "V1" else g.BOUNDARY_V2
+    x0 = si.boundary_data(level, 81)
+    b = si.rhs(level, 82)
+    out = []
+    for values in [g.VALUES_ON_THE_FLY, g.VALUES_TABULATED]:
+        t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=g.F64, boundary=bnd,
+                  slabs=slabs, values=values)
+        xd, bd = dev(x0, torch.float64), dev(b, torch.float64)
+        n1 = t.smooth(xd, bd, 2, norms=True)
+        # re-import scaled coefficients: the tables must follow them
+        c = t.export_surrogate()
+        t.import_surrogate(c * (1.0 + 1e-3))
+        n2 = t.smooth(xd, bd, 1, norms=True)
+        out.append((xd.cpu().numpy(), n1, n2))
+        t.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
 @pytest.mark.parametrize("level,kind,prec", [(3, "const", "F64"), (4, "sinprod", "F64"), (5, "kappa_i", "F64"),
                                              (6, "sinprod", "F64"), (5, "sinprod", "MIXED"), (7, "const", "MIXED"),
                                              (6, "kappa_i", "F32")])

@@ -173,3 +173,21 @@ def test_v1_keeps_the_fit_and_rejects_band_kernels(g):
     assert e.value.status == g.ILU_EINVAL
     with pytest.raises(g.IluError):
         g.Tet(P, 5, poly_degree=4, device=-1, boundary=5)
+
+
+def test_tabulated_values_are_an_fp64_option(g):
+    """ilu_opts.values: TABULATED needs F64 and level <= 9; unknown values
+    are rejected before any device work."""
+    P = si.macro_tet(36)
+    g.Tet(P, 4, poly_degree=2, device=-1, precision=g.F64, values=g.VALUES_TABULATED).close()
+    g.Tet(P, 4, poly_degree=2, device=-1, precision=g.MIXED, values=g.VALUES_ON_THE_FLY).close()
+    for prec in [g.MIXED, g.F32]:
+        with pytest.raises(g.IluError) as e:
+            g.Tet(P, 4, poly_degree=2, device=-1, precision=prec, values=g.VALUES_TABULATED)
+        assert e.value.status == g.ILU_EINVAL
+    with pytest.raises(g.IluError) as e:
+        g.Tet(P, 10, poly_degree=2, device=-1, precision=g.F64, values=g.VALUES_TABULATED)
+    assert e.value.status == g.ILU_EINVAL
+    with pytest.raises(g.IluError) as e:
+        g.Tet(P, 4, poly_degree=2, device=-1, precision=g.F64, values=3)
+    assert e.value.status == g.ILU_EINVAL

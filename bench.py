@@ -172,6 +172,23 @@ class ClockSampler:
         return out
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: every rank gets the maximum (one MAX
+    all-reduce; `dist` None for a single process)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, dof_per_rank, steps, total_ms):
+    """Whole-job throughput of `world` replicas that each swept `dof_per_rank`
+    interior points `steps` times, over the slowest rank's time."""
+    return world * dof_per_rank * steps / (total_ms / 1e3)
+
+
 def cpu_oracle_sample(steps=8, warmup=0):
     """The oracle, as it stands, on the same workload: set-up (untimed), then
     `warmup` untimed and `steps` timed matrix-free sweeps, each = evaluate the
@@ -652,11 +669,8 @@ def main():
     total_ms = sum(ms_steps)
     kms, launches = t.profile_read()
     t.profile(False)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * interior(LEVEL) * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_rate(world, interior(LEVEL), K, total_ms)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     xh = np.zeros(nn)

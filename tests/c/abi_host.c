@@ -62,6 +62,13 @@ int main(void) {
   CHECK(ilu_setup(P, 11, &k, 3, &o, &t) == ILU_EINVAL, "level out of range");
   o.boundary = 7;
   CHECK(ilu_setup(P, 4, &k, 3, &o, &t) == ILU_EINVAL, "unknown boundary variant");
+  o.boundary = ILU_BOUNDARY_V2;
+  o.values = ILU_VALUES_TABULATED; /* an FP64 option */
+  CHECK(ilu_setup(P, 4, &k, 3, &o, &t) == ILU_EINVAL, "tabulated values rejected for MIXED");
+  o.precision = ILU_F64;
+  CHECK(ilu_setup(P, 4, &k, 3, &o, &t) == ILU_OK && t != NULL, "tabulated values accepted for F64");
+  ilu_destroy(t);
+  t = NULL;
   CHECK(strlen(ilu_version()) > 0, "version");
   return fails ? 1 : 0;
 }

@@ -199,8 +199,13 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
 ilu_status ilu_destroy(ilu_tet t);
 
 /* Replace the fitted surrogate by externally supplied coefficients (same
- * layout as ilu_export_surrogate) and rebuild the evaluation tables.  Lets a
- * caller run the sweep with surrogates fitted elsewhere. */
+ * layout as ilu_export_surrogate) and rebuild the evaluation tables (and the
+ * tabulated values of an F64 handle).  Lets a caller run the sweep with
+ * surrogates fitted elsewhere.  Synchronous; must not overlap a sweep of the
+ * same handle on another stream.
+ * Errors: ILU_EINVAL (count, non-finite value), ILU_ESINGULAR (1/D~ <= 0
+ * somewhere; the previous coefficients stay), ILU_ECUDA (the upload failed:
+ * the handle is marked failed). */
 ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n);
 
 /* Copy the surrogate coefficients to host memory: 8 blocks (w s se bnw bn bc

@@ -807,6 +807,7 @@ ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(coefs[i])) return fail(ILU_EINVAL, "non-finite coefficient");
   std::lock_guard<std::mutex> lk(t->mu);
+  if (t->device >= 0 && t->failed) return fail(ILU_ECUDA, "handle failed earlier; destroy it");
   std::vector<double> old = t->host.coefs;
   std::memcpy(t->host.coefs.data(), coefs, sizeof(double) * n);
   build_row_tables(t->host);
@@ -816,7 +817,11 @@ ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n) {
     build_row_tables(t->host);
     return st;
   }
-  if (t->device >= 0) return upload_tables(t);
+  if (t->device >= 0) {
+    st = upload_tables(t);  // device tables (and tabulated values) now disagree with the host: unusable
+    if (st != ILU_OK) t->failed = true;
+    return st;
+  }
   return ILU_OK;
 }
 

@@ -196,3 +196,22 @@ def test_table2_pin_catches_planted_mistakes(orc, mg, table2):
     for name, make in planted.items():
         rho = rate(make)
         assert abs(rho - 0.025) > tol, (name, rho)
+
+
+def test_height_sweep_follows_the_paper(orc, mg):
+    """The paper's height study (Sec. 4.2, the figure on a trirectangular tet
+    whose top vertex sinks): with symmetric Gauss-Seidel smoothing the
+    V(3,3)-cycle rate degenerates as the height shrinks; with ILU(0) it stays
+    robust and tends to an exact solver; the ratio log(rho_ILU)/log(rho_SGS),
+    the extra cycles SGS needs, grows without bound."""
+    _, nint = orc.interior_ids(64)
+    e0 = np.random.default_rng(5).uniform(-1, 1, nint)
+    ilu, sgs = [], []
+    for h in [1.0, 0.25, 1.0 / 16]:
+        P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, h]], dtype=float)
+        ilu.append(mg.Hierarchy(P, 6, smoother="ilu").rate(e0)[0])
+        sgs.append(mg.Hierarchy(P, 6, smoother="sgs").rate(e0)[0])
+    assert sgs[0] < sgs[1] < sgs[2] and sgs[2] > 0.7, sgs
+    assert ilu[0] > ilu[1] > ilu[2] and ilu[0] < 0.05 and ilu[2] < 1e-3, ilu
+    ratio = [np.log(a) / np.log(b) for a, b in zip(ilu, sgs)]
+    assert ratio[0] < ratio[1] < ratio[2] and ratio[2] > 20, ratio

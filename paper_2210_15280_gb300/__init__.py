@@ -224,7 +224,18 @@ def lfa_order(macro_tet):
     return [int(v) for v in perm], float(mu[0]), mus
 
 
-class Tet:
+class _Handle:
+    """`with` support for the handle classes: the handle is released on exit."""
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
+
+class Tet(_Handle):
     """One macro-tetrahedron set up for smoothing (wraps an ilu_tet handle)."""
 
     def __init__(self, macro_tet, level, coeff=None, poly_degree=4, **opts):
@@ -336,7 +347,7 @@ class _Borrowed(Tet):
         self.h = None
 
 
-class Multigrid:
+class Multigrid(_Handle):
     """Geometric multigrid V-cycle on one macro-tet, levels 2..level, with the
     surrogate smoother on levels >= 3 (wraps an ilu_mg handle)."""
 
@@ -392,7 +403,7 @@ class Multigrid:
         return rho.value, hist
 
 
-class Batch:
+class Batch(_Handle):
     """Tets smoothed together (wraps an ilu_batch handle).  Keeps the Tet
     objects alive for as long as the batch exists."""
 
@@ -423,7 +434,7 @@ class Batch:
         _check(lib().ilu_batch_smooth(self.h, xa, ba, int(sweeps), _stream(stream)))
 
 
-class Server:
+class Server(_Handle):
     """The request loop (wraps an ilu_server handle): submit interior solves,
     wait for their results; the loop admits them by free device memory and
     runs admitted solves concurrently."""

@@ -191,3 +191,11 @@ def test_tabulated_values_are_an_fp64_option(g):
     with pytest.raises(g.IluError) as e:
         g.Tet(P, 4, poly_degree=2, device=-1, precision=g.F64, values=3)
     assert e.value.status == g.ILU_EINVAL
+
+
+def test_handles_close_on_with_exit(g):
+    P = si.macro_tet(37)
+    with g.Tet(P, 3, poly_degree=2, device=-1) as t:
+        assert t.h
+        n = len(t.export_surrogate())
+    assert t.h is None and n == 8 * 27

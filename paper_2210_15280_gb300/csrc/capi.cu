@@ -13,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ilu.h"
@@ -417,17 +418,29 @@ ilu_status upload_tables(ilu_tet t) {
 }
 
 // the surrogate pivot inverse must be positive everywhere for L~ D~ L~^T to
-// be symmetric positive definite
+// be symmetric positive definite (every interior point checked, face layers
+// shared out over host threads)
 ilu_status check_surrogate(const HostTet &h) {
   const int N = h.N;
-  for (int z = 1; z <= N - 3; ++z)
-    for (int y = 1; y <= N - 2 - z; ++y)
-      for (int x = 1; x <= N - 1 - y - z; ++x) {
-        double v[8];
-        host_eval_tables(h, x, y, z, v);
-        if (!(v[7] > 0.0) || !std::isfinite(v[7]))
-          return fail(ILU_ESINGULAR, "surrogate 1/D is not positive at an interior point");
-      }
+  const int nth = std::max(1, std::min<int>(16, (int)std::thread::hardware_concurrency()));
+  std::vector<char> bad(nth, 0);
+  auto work = [&](int k) {
+    for (int z = 1 + k; z <= N - 3 && !bad[k]; z += nth)
+      for (int y = 1; y <= N - 2 - z; ++y)
+        for (int x = 1; x <= N - 1 - y - z; ++x) {
+          double v[8];
+          host_eval_tables(h, x, y, z, v);
+          if (!(v[7] > 0.0) || !std::isfinite(v[7])) {
+            bad[k] = 1;
+            return;
+          }
+        }
+  };
+  std::vector<std::thread> pool;
+  for (int k = 0; k < nth; ++k) pool.emplace_back(work, k);
+  for (auto &th : pool) th.join();
+  for (char b : bad)
+    if (b) return fail(ILU_ESINGULAR, "surrogate 1/D is not positive at an interior point");
   return ILU_OK;
 }
 

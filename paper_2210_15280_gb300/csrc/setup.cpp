@@ -377,6 +377,9 @@ struct Sample {
 // Streaming factorisation + samples.  Layer buffers hold, for every (x, y) of
 // the current and the previous face layer, the 7 factor entries and the pivot
 // (defaults L = 0, D = 1 off the interior, as Alg. 1 initialises them).
+// The recursion is sequential in lexicographic order.  The operator stencils
+// it consumes are not: for a variable coefficient, worker threads assemble
+// the stencils of face layer z + 1 while this thread factors layer z.
 static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::string &err) {
   const int N = t.N;
   const int S = N + 2;
@@ -392,23 +395,57 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
   reset(lay[0]);
   reset(lay[1]);
   const int stride = std::max(1, 1 << std::max(0, t.L - t.LH));
+  const int smask = stride - 1;  // stride is a power of two: v mod stride = v & smask, also for v < 0
   const int64_t nint = grid_interior(N);
   if (t.keep_exact) {
     t.exactL.assign((size_t)7 * nint, 0.0);
     t.exactD.assign((size_t)nint, 0.0);
   }
-  auto mod = [](int v, int s) { return ((v % s) + s) % s; };
+  // the stencil of R_t A R_t^T at an interior point: A with the couplings to
+  // non-interior points removed (only cell-boundary points have any)
+  auto stencil = [&](int x, int y, int z, double *A) {
+    host_stencil(t, x, y, z, A);
+    if (on_cell_boundary(N, x, y, z))
+      for (int d = 0; d < 15; ++d)
+        if (!in_interior(N, x + dir_dx(d), y + dir_dy(d), z + dir_dz(d))) A[d] = 0.0;
+  };
+  // variable coefficient: stencils of a whole face layer, 15 per point, rows
+  // in order; row y of layer z starts at point (y - 1)(N - 1 - z) - (y - 1) y / 2
+  const bool pre = !t.const_kappa;
+  const int nworkers = pre ? std::max(1, std::min<int>(15, (int)std::thread::hardware_concurrency() - 1)) : 0;
+  auto row_start = [&](int y, int z) { return (size_t)(y - 1) * (N - 1 - z) - (size_t)(y - 1) * y / 2; };
+  std::vector<double> stn[2];
+  auto assemble = [&](int z, int part, int parts) {
+    std::vector<double> &buf = stn[z & 1];
+    for (int y = 1 + part; y <= N - 2 - z; y += parts)
+      for (int x = 1; x <= N - 1 - y - z; ++x) stencil(x, y, z, &buf[(row_start(y, z) + x - 1) * 15]);
+  };
+  if (pre) {
+    const size_t cap = (size_t)(N - 3) * (N - 2) / 2 * 15;  // points of the largest layer (z = 1), x 15
+    stn[0].assign(cap, 0.0);
+    stn[1].assign(cap, 0.0);
+    if (N - 3 >= 1) {
+      std::vector<std::thread> w;
+      for (int k = 0; k < nworkers; ++k) w.emplace_back(assemble, 1, k, nworkers);
+      for (auto &th : w) th.join();
+    }
+  }
+  const bool ilu = t.factor == ILU_FACTOR_ILU0;
   int64_t i = 0;
   for (int z = 1; z <= N - 3; ++z) {
+    std::vector<std::thread> workers;  // the next layer's stencils, meanwhile
+    if (pre && z + 1 <= N - 3)
+      for (int k = 0; k < nworkers; ++k) workers.emplace_back(assemble, z + 1, k, nworkers);
     std::vector<double> &cur = lay[z & 1];
     const std::vector<double> &prv = lay[(z - 1) & 1];
     reset(cur);
-    for (int y = 1; y <= N - 2 - z; ++y)
+    ilu_status st = ILU_OK;
+    for (int y = 1; y <= N - 2 - z && st == ILU_OK; ++y)
       for (int x = 1; x <= N - 1 - y - z; ++x, ++i) {
-        double A[15];
-        host_stencil(t, x, y, z, A);
-        for (int d = 0; d < 15; ++d)
-          if (!in_interior(N, x + dir_dx(d), y + dir_dy(d), z + dir_dz(d))) A[d] = 0.0;
+        double Aloc[15];
+        const double *A = Aloc;
+        if (pre) A = &stn[z & 1][(row_start(y, z) + x - 1) * 15];
+        else stencil(x, y, z, Aloc);
         // neighbour factor rows p + d for d in D_l
         const double *nb[7];
         for (int d = 0; d < 7; ++d) {
@@ -417,7 +454,6 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
         }
         // symmetric Gauss-Seidel keeps the first term of each recursion: the
         // neighbour's stored pivot is then its diagonal entry a(p+d, p+d)
-        const bool ilu = t.factor == ILU_FACTOR_ILU0;
         double Lp[7];
         for (int k = 0; k < 7; ++k) {
           const int d = pl.order[k];
@@ -434,7 +470,8 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
           for (int d = 0; d < 7; ++d) Dp -= Lp[d] * Lp[d] * nb[d][7];
         if (!(Dp > 0.0)) {
           err = ilu ? "non-positive ILU(0) pivot" : "non-positive diagonal entry";
-          return ILU_ESINGULAR;
+          st = ILU_ESINGULAR;
+          break;
         }
         double *me = &cur[((size_t)y * S + x) * 8];
         for (int d = 0; d < 7; ++d) me[d] = Lp[d];
@@ -449,11 +486,13 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
         }
         for (int f = 0; f < 8; ++f) {
           const int dx = f < 7 ? dir_dx(f) : 0, dy = f < 7 ? dir_dy(f) : 0, dz = f < 7 ? dir_dz(f) : 0;
-          if (mod(x - 1 + dx, stride) || mod(y - 1 + dy, stride) || mod(z - 1 + dz, stride)) continue;
+          if (((x - 1 + dx) & smask) || ((y - 1 + dy) & smask) || ((z - 1 + dz) & smask)) continue;
           if (f < 7 && !in_interior(N, x + dx, y + dy, z + dz)) continue;
           samples[f].push_back({x, y, z, f < 7 ? Lp[f] : 1.0 / Dp});
         }
       }
+    for (auto &th : workers) th.join();
+    if (st != ILU_OK) return st;
   }
   return ILU_OK;
 }

@@ -436,9 +436,13 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
     std::vector<std::thread> workers;  // the next layer's stencils, meanwhile
     if (pre && z + 1 <= N - 3)
       for (int k = 0; k < nworkers; ++k) workers.emplace_back(assemble, z + 1, k, nworkers);
+    // No per-layer reset: the recursion reads non-interior neighbours only
+    // at x = 0 or y = 0 (never written) or in layer 0 (the first buffer, never
+    // written before layer 2 starts); every other neighbour it reads is an
+    // interior point computed earlier, and entries left over from layer z - 2
+    // lie beyond this layer's diagonal x + y = N - 1 - z, where nothing reads.
     std::vector<double> &cur = lay[z & 1];
     const std::vector<double> &prv = lay[(z - 1) & 1];
-    reset(cur);
     ilu_status st = ILU_OK;
     for (int y = 1; y <= N - 2 - z && st == ILU_OK; ++y)
       for (int x = 1; x <= N - 1 - y - z; ++x, ++i) {

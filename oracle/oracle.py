@@ -289,14 +289,72 @@ def cell_boundary_mask(N):
     return (c[:, 0] == 1) | (c[:, 1] == 1) | (c[:, 2] == 1) | (c.sum(axis=1) == N - 1)
 
 
-def v1_factors(N, L_sur, L_exact):
-    """Boundary variant V1 (Sec. 4.1, Alg. 2): the exact ILU(0) factor at the
-    cell-boundary points, the surrogate elsewhere.  D~^-1 stays the
-    surrogate's.  Alg. 2 applied with this field is the V1 smoother."""
+def v1_factors(N, L_sur, Dinv_sur, L_exact, D_exact):
+    """Boundary variant V1 (Sec. 4.1, Alg. 1): at the cell-boundary points the
+    exact ILU(0) factors stored by the factorisation replace the surrogates,
+    elsewhere the surrogates stay.  Both stored fields are used: L^p_d
+    (d in D_l) and the multiplicative inverse 1/D^p of the centre, which
+    Alg. 1 stores for V1 next to the L entries and which the V1 description
+    of Sec. 4.1 says the substitutions use.  Returns (L, Dinv); Alg. 2 applied
+    with these fields is the V1 smoother."""
     m = cell_boundary_mask(N)
     L = np.array(L_sur, dtype=np.float64, copy=True)
     L[:, m] = L_exact[:, m]
-    return L
+    Dinv = np.array(Dinv_sur, dtype=np.float64, copy=True)
+    Dinv[m] = 1.0 / np.asarray(D_exact, dtype=np.float64)[m]
+    return L, Dinv
+
+
+# direction vectors of D in the order of DIRS (Sec. 2.1, with b = z-1, t = z+1)
+DVEC = [(-1, 0, 0), (0, -1, 0), (1, -1, 0), (-1, 1, -1), (0, 1, -1), (0, 0, -1), (1, 0, -1), (0, 0, 0),
+        (1, 0, 0), (0, 1, 0), (-1, 1, 0), (1, -1, 1), (0, -1, 1), (0, 0, 1), (-1, 0, 1)]
+
+
+def _interior(N, q):
+    return q[0] >= 1 and q[1] >= 1 and q[2] >= 1 and q[0] + q[1] + q[2] <= N - 1
+
+
+def local_residual(P, N, coeff, x_at, b_at, p):
+    """r_p = b_p - sum_{d in D} A^p_d x^{p+d} at one interior point p
+    (Alg. 2, all 15 directions, boundary x = Dirichlet data), with the
+    element-assembled stencil of p; x_at, b_at map a point to its value."""
+    A = local_stencil(P, N, p, coeff)
+    r = b_at(p)
+    for d, v in enumerate(DVEC):
+        r -= A[d] * x_at((p[0] + v[0], p[1] + v[1], p[2] + v[2]))
+    return r
+
+
+def ldlt_apply_at(N, deg, coefs, w_at, p, cache=None):
+    """(L~ D~ L~^T w)_p at one interior point p for the surrogate factors
+    with the V2 rule (Sec. 3, Alg. 2): L~ unit lower triangular with
+    L~_{q, q+d} = L~^q_d (d in D_l, zero where q+d is not interior),
+    D~ = diag(1 / D~^-1), every value from the surrogate polynomials (direct
+    tensor evaluation).  w_at maps an interior point to w there.  The smoother
+    solves C~ w = r, so at every p this equals r_p."""
+    cache = {} if cache is None else cache
+
+    def vals(q):  # L~^q_d (d in D_l) and D~^-1(q), unmasked
+        v = cache.get(q)
+        if v is None:
+            v = [surrogate_eval(N, deg, coefs[f], q) for f in range(8)]
+            cache[q] = v
+        return v
+
+    def lt_w(q):  # (L~^T w)_q = w_q + sum_{d in D_l, q-d interior} L~^{q-d}_d w_{q-d}
+        s = w_at(q)
+        for d in range(7):
+            m = (q[0] - DVEC[d][0], q[1] - DVEC[d][1], q[2] - DVEC[d][2])
+            if _interior(N, m):
+                s += vals(m)[d] * w_at(m)
+        return s
+
+    out = lt_w(p) / vals(p)[7]
+    for d in range(7):
+        q = (p[0] + DVEC[d][0], p[1] + DVEC[d][1], p[2] + DVEC[d][2])
+        if _interior(N, q):
+            out += vals(p)[d] * lt_w(q) / vals(q)[7]
+    return out
 
 
 # ------------------------------------------------------------ smoother ---

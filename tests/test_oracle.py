@@ -538,10 +538,63 @@ def test_cell_boundary_mask_is_the_points_with_an_outside_neighbour(orc, level):
 
 
 def test_v1_with_exact_factors_is_the_exact_smoother(orc):
-    """With the surrogate replaced by the exact factor, V1 changes nothing."""
+    """With the surrogate replaced by the exact factors, V1 changes nothing;
+    with zero surrogates, exactly the cell-boundary points carry the stored
+    factors L^p_d and 1/D^p (Sec. 4.1, Alg. 1)."""
     pr = orc.Problem(si.macro_tet(31), 4)
-    L1 = orc.v1_factors(pr.N, pr.L, pr.L)
-    assert np.array_equal(L1, pr.L)
-    Lx = orc.v1_factors(pr.N, np.zeros_like(pr.L), pr.L)
+    L1, D1 = orc.v1_factors(pr.N, pr.L, 1.0 / pr.D, pr.L, pr.D)
+    assert np.array_equal(L1, pr.L) and np.array_equal(D1, 1.0 / pr.D)
+    Lx, Dx = orc.v1_factors(pr.N, np.zeros_like(pr.L), np.zeros_like(pr.D), pr.L, pr.D)
     m = orc.cell_boundary_mask(pr.N)
     assert np.array_equal(Lx[:, m], pr.L[:, m]) and not Lx[:, ~m].any()
+    assert np.array_equal(Dx[m], 1.0 / pr.D[m]) and not Dx[~m].any()
+
+
+def test_v1_at_level_2_solves_in_one_sweep_whatever_the_surrogate(orc):
+    """Level 2 has one interior point, on the cell boundary, whose exact
+    factor is D = A_c.  V1 stores 1/D there, so one V1 sweep solves the
+    problem exactly however wrong the surrogate is.  The same sweep with the
+    surrogate's D~^-1 (the planted mistake of not using the stored centre)
+    does not."""
+    P = si.macro_tet(32)
+    pr = orc.Problem(P, 2)
+    N = pr.N
+    bad_L = np.full_like(pr.L, 0.3)
+    bad_Dinv = 0.5 / pr.D
+    x0 = si.boundary_data(2, 33)
+    b = si.rhs(2, 34)
+    L1, D1 = orc.v1_factors(N, bad_L, bad_Dinv, pr.L, pr.D)
+    x = orc.smooth(pr.A, N, L1, D1, x0.copy(), b, 1)
+    assert orc.residual(pr.A, N, x, b)[1] <= 1e-14 * max(1.0, np.abs(b).max())
+    wrong = orc.smooth(pr.A, N, L1, bad_Dinv, x0.copy(), b, 1)
+    assert orc.residual(pr.A, N, wrong, b)[1] > 1e-3 * orc.residual(pr.A, N, x0, b)[1]
+
+def test_local_ldlt_apply_recovers_the_residual_of_one_sweep(orc):
+    """One oracle sweep x1 = x0 + C~^-1 r; the point-local (L~ D~ L~^T w)_p of
+    w = x1 - x0, evaluated from the surrogate polynomials, equals the point's
+    residual r_p at every interior point, and local_residual equals the
+    assembled residual.  A dropped backward term is caught."""
+    level, deg = 4, [3, 3, 3]
+    P = si.macro_tet(35)
+    co = orc.Coeff("sinprod", 1.0, 0.5)
+    pr = orc.Problem(P, level, co, deg=deg)
+    N = pr.N
+    x0 = si.boundary_data(level, 36)
+    b = si.rhs(level, 37)
+    Ls, Dinv = pr.surrogate_factors()
+    x1 = orc.smooth(pr.A, N, Ls, Dinv, x0.copy(), b, 1)
+    r, _ = orc.residual(pr.A, N, x0, b)
+    w = x1 - x0
+    at = lambda v: (lambda q: v[orc.index(N, *q)])
+    cache = {}
+    worst = 0.0
+    for q in map(tuple, orc.interior_coords(N)):
+        got = orc.ldlt_apply_at(N, deg, pr.coefs, at(w), q, cache)
+        worst = max(worst, abs(got - r[orc.index(N, *q)]))
+        assert abs(orc.local_residual(P, N, co, at(x0), at(b), q) - r[orc.index(N, *q)]) < 1e-12
+    assert worst < 1e-11 * np.abs(r).max()
+    # planted mistake: w with one backward term dropped (w at its neighbour perturbed)
+    q0 = (2, 2, 2)
+    wp = w.copy()
+    wp[orc.index(N, 3, 2, 2)] *= 1.01
+    assert abs(orc.ldlt_apply_at(N, deg, pr.coefs, at(wp), q0) - r[orc.index(N, *q0)]) > 1e-6 * np.abs(r).max()

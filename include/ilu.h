@@ -29,6 +29,8 @@
  * Errors.  Every entry point returns an ilu_status; no exception crosses the
  *   ABI.  ilu_last_error() gives a thread-local message for the last failure.
  *   ILU_ECUDA and ILU_ETIMEOUT leave the handle unusable: destroy it.
+ * Devices.  A call may switch the calling thread to its handle's device while
+ *   it runs; it puts the thread's current device back before it returns.
  */
 #ifndef ILU_H
 #define ILU_H
@@ -94,12 +96,14 @@ typedef struct {
  *                    not interior is set to 0 in the substitutions (default);
  *   ILU_BOUNDARY_V1  at the interior points on the cell boundary (x = 1,
  *                    y = 1, z = 1 or x + y + z = N - 1) the exact ILU(0)
- *                    entries L^p_d, d in D_l, computed by Alg. 1 at set-up,
- *                    are stored (7 values per such point, O(N^2) in all) and
- *                    used instead of the surrogates: by the forward
- *                    substitution at p, by the backward one wherever p - d
- *                    is such a point.  D~^-1 stays a surrogate (Alg. 2).
- *                    Uses the slab substitution kernels. */
+ *                    entries L^p_d, d in D_l, and 1/D^p computed by Alg. 1
+ *                    at set-up are stored (8 values per such point, O(N^2)
+ *                    in all) and used instead of the surrogates: L^p_d by
+ *                    the forward substitution at p and by the backward one
+ *                    wherever p - d is such a point, 1/D^p by the backward
+ *                    one at p (Alg. 1 stores 1/beta_c for V1 and Sec. 4.1
+ *                    has the stored stencils used by both substitutions).
+ *                    Either substitution kernel family. */
 typedef enum { ILU_BOUNDARY_V2 = 0, ILU_BOUNDARY_V1 = 1 } ilu_boundary;
 
 /* Which vertex order of the macro-tetrahedron the handle uses (Sec. 3):
@@ -273,13 +277,15 @@ ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double
  * library allocate device memory (a framework's caching allocator or a fixed
  * serving pool owns it, or cudaMalloc's implicit synchronisation is not
  * acceptable).  The paper has no counterpart.  The caller passes x, b (device,
- * the handle's vector type), r (device, same type; required: boundary entries
- * set to 0) and norm_dev (device, one double receiving ||r||_2).  The only
+ * the handle's vector type), r (device, same type; required; the call sets its
+ * boundary entries to 0) and norm_dev (device, one double receiving ||r||_2).  The only
  * scratch, the per-block partial sums of the norm, lives in a fixed 1 MiB
  * device array inside the library: levels above 9 are rejected with
  * ILU_EINVAL.  The array is shared by all calls on a device and keeps the last
  * call's contents (every entry used is written before it is read); calls whose
- * kernels overlap on the GPU race on it and must be serialised.  The first
+ * kernels overlap on the GPU race on it and must be serialised. Host-only
+ * handles are refused with ILU_ENODEV and failed ones with ILU_ECUDA, as
+ * everywhere; the call holds the handle's lock while it launches.  The first
  * call on a device looks up the array's device address; make that first call
  * before any stream capture.  Asynchronous on `stream`; calls no allocator. */
 ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void *b, void *r, double *norm_dev, void *stream);

@@ -267,7 +267,7 @@ __device__ __forceinline__ int owner_of(const BatchMap &bm, int ticket) {
 
 // ------------------------------------------------------------ forward --
 
-template <int DXP, int REG>
+template <int DXP, int REG, bool V1>
 __global__ void __launch_bounds__(256, 2) fwd_band(const DevTet *__restrict__ tets, BatchMap bm,
                                                    LaunchStatus *status, long long max_spins) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -410,6 +410,14 @@ __global__ void __launch_bounds__(256, 2) fwd_band(const DevTet *__restrict__ te
       // away (V2), the previous step of this row goes last (shortest chain)
       float L[8];
       C.eval((float)(2 * x - (N - y - z)) * hh, L);
+      if constexpr (V1) {  // boundary variant V1: the stored exact L^p_d at a cell-boundary point p
+        const float *bndv = reinterpret_cast<const float *>(t.bnd);
+        if (bndv && act && on_cell_boundary(N, x, y, z)) {
+          const float *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, y, z) * 8;
+#pragma unroll
+          for (int d = 0; d < 7; ++d) L[d] = rec[d];
+        }
+      }
       const float zero = 0.f;
       ws = y >= 2 ? ws : zero;
       wse = y >= 2 ? wse : zero;
@@ -467,7 +475,7 @@ __global__ void __launch_bounds__(256, 2) fwd_band(const DevTet *__restrict__ te
 // w^p <- D~^{-1}(p) w^p - sum_{d in D_l, p-d interior} L~^{p-d}_d w^{p-d},
 // in decreasing step order; the result stays in the band array (x is
 // updated by band_update_kernel).
-template <int DXP, int REG>
+template <int DXP, int REG, bool V1>
 __global__ void __launch_bounds__(256, 2) bwd_band(const DevTet *__restrict__ tets, BatchMap bm,
                                                    LaunchStatus *status, long long max_spins) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -609,6 +617,18 @@ __global__ void __launch_bounds__(256, 2) bwd_band(const DevTet *__restrict__ te
       // lane evaluates, terms of neighbours outside the interior are selected away
       float L[8];
       C.eval((float)(2 * x - (N - y - z)) * hh, L);
+      if constexpr (V1) {  // V1: stored exact 1/D^p at p and L^{p-d}_d where p - d is a cell-boundary point
+        const float *bndv = reinterpret_cast<const float *>(t.bnd);
+        if (bndv && act) {
+          if (on_cell_boundary(N, x, y, z)) L[0] = bndv[(size_t)bnd_record(t.bnd_off, N, x, y, z) * 8 + 7];
+#pragma unroll
+          for (int d = 0; d < kNumLower; ++d) {
+            const int qx = x - dir_dx(d), qy = y - dir_dy(d), qz = z - dir_dz(d);
+            if (in_interior(N, qx, qy, qz) && on_cell_boundary(N, qx, qy, qz))
+              L[1 + d] = bndv[(size_t)bnd_record(t.bnd_off, N, qx, qy, qz) * 8 + d];
+          }
+        }
+      }
       const float zero = 0.f;
       wn = inner ? wn : zero;                                  // p - s   = (x, y+1, z)
       wtc = inner ? wtc : zero;                                // p - bc  = (x, y, z+1)
@@ -837,13 +857,18 @@ __global__ void __launch_bounds__(256) band_update_kernel(const DevTet *__restri
   }
 }
 
-template <int DXP, int REG>
-cudaError_t launch_fb(bool fwd, const BandLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st) {
-  auto kernel = fwd ? fwd_band<DXP, REG> : bwd_band<DXP, REG>;
+template <int DXP, int REG, bool V1>
+cudaError_t launch_fb1(bool fwd, const BandLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st) {
+  auto kernel = fwd ? fwd_band<DXP, REG, V1> : bwd_band<DXP, REG, V1>;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem_bytes(8));
   if (e != cudaSuccess) return e;
   kernel<<<L.ctas, L.Z * 32, band_smem_bytes(L.Z), st>>>(L.tets, fwd ? L.map_f : L.map_b, status, max_spins);
   return cudaGetLastError();
+}
+template <int DXP, int REG>
+cudaError_t launch_fb(bool fwd, const BandLaunch &L, LaunchStatus *status, long long max_spins, cudaStream_t st) {
+  return L.v1 ? launch_fb1<DXP, REG, true>(fwd, L, status, max_spins, st)
+              : launch_fb1<DXP, REG, false>(fwd, L, status, max_spins, st);
 }
 
 }  // namespace

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "../../include/ilu.h"
+#include "hooks.h"
 #include "kernels.cuh"
 
 using namespace ilu;
@@ -369,6 +370,7 @@ ilu_status capture(ilu_batch b, int sweeps) {
 extern "C" {
 
 ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, ilu_batch *out) {
+  ilu::DeviceRestore keep_device;
   if (!out) return fail(ILU_EINVAL, "null output handle");
   *out = nullptr;
   if (!tets || n <= 0) return fail(ILU_EINVAL, "empty batch");
@@ -417,12 +419,14 @@ ilu_status ilu_batch_create(const ilu_tet *tets, int n, const ilu_opts *opts, il
 }
 
 ilu_status ilu_batch_destroy(ilu_batch b) {
+  ilu::DeviceRestore keep_device;
   if (!b) return ILU_OK;
   release(b);
   return ILU_OK;
 }
 
 ilu_status ilu_batch_smooth(ilu_batch b, void *const *x, const void *const *bv, int sweeps, void *stream) {
+  ilu::DeviceRestore keep_device;
   if (!b || !x || !bv) return fail(ILU_EINVAL, "null argument");
   if (b->failed) return fail(ILU_ECUDA, "batch failed earlier; destroy it");
   if (sweeps < 0) return fail(ILU_EINVAL, "negative sweep count");

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ilu.h"
+#include "hooks.h"
 #include "kernels.cuh"
 #include "setup.h"
 
@@ -291,6 +292,7 @@ ilu_status upload_band(ilu_tet t, int requested_slabs) {
   L.ctas = t->band_ncta;
   L.Z = Z;
   L.reg = t->host.dx;
+  L.v1 = t->host.boundary == ILU_BOUNDARY_V1;
   L.map_f = {t->d_bint + at_map, t->d_bint + at_map + 2, 1, t->d_flags + t->dev.fwd.ticket, nullptr, nullptr};
   L.map_b = {t->d_bint + at_map, t->d_bint + at_map + 2, 1, t->d_flags + t->dev.bwd.ticket, nullptr, nullptr};
   t->band_tprefix = t->d_bint + at_tp;
@@ -337,7 +339,7 @@ ilu_status upload(ilu_tet t) {
   CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
   // band kernels: measured faster than the slab kernels from level 9 on
   // (L7/L8/L9 MIXED sweeps: 0.78/1.77/10.2 ms slab, 1.10/2.19/6.0 ms band)
-  t->use_band = t->precision != ILU_F64 && h.boundary == ILU_BOUNDARY_V2 && wave_uses_registers(t->kind(), h.dx) &&
+  t->use_band = t->precision != ILU_F64 && wave_uses_registers(t->kind(), h.dx) &&
                 (t->kernel_choice == ILU_KERNEL_BAND || (t->kernel_choice == ILU_KERNEL_AUTO && h.L >= 9));
   if (t->use_band) {
     ilu_status bs = upload_band(t, t->requested_slabs);
@@ -624,6 +626,13 @@ const DevTet *tet_dev_view(ilu_tet t, int *device, int *precision, size_t *nnode
   *nnodes = t->nnodes();
   return t->device >= 0 ? &t->dev : nullptr;
 }
+ilu_status tet_acquire(ilu_tet t, std::unique_lock<std::mutex> *lk) {
+  const ilu_status st = check_usable(t);
+  if (st != ILU_OK) return st;
+  *lk = std::unique_lock<std::mutex>(t->mu);
+  return t->failed ? fail(ILU_ECUDA, "handle failed earlier; destroy it") : ILU_OK;
+}
+void tet_mark_failed(ilu_tet t) { t->failed = true; }
 void set_last_error(const std::string &msg) { g_err = msg; }
 bool tet_view(ilu_tet t, TetView *v) {
   if (!t || t->device < 0) return false;
@@ -710,6 +719,7 @@ long long ilu_index(int level, int x, int y, int z) {
 
 ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coeff, int poly_degree,
                      const ilu_opts *opts, ilu_tet *out) {
+  ilu::DeviceRestore keep_device;
   if (!out) return fail(ILU_EINVAL, "null output handle");
   *out = nullptr;
   if (!macro_tet) return fail(ILU_EINVAL, "null macro_tet");
@@ -722,8 +732,6 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   if (o.stencil < ILU_STENCIL_AUTO || o.stencil > ILU_STENCIL_STORED) return fail(ILU_EINVAL, "unknown stencil choice");
   if (o.orient != ILU_ORIENT_GIVEN && o.orient != ILU_ORIENT_LFA) return fail(ILU_EINVAL, "unknown orientation choice");
   if (o.boundary != ILU_BOUNDARY_V2 && o.boundary != ILU_BOUNDARY_V1) return fail(ILU_EINVAL, "unknown boundary variant");
-  if (o.boundary == ILU_BOUNDARY_V1 && o.kernel == ILU_KERNEL_BAND)
-    return fail(ILU_EINVAL, "boundary variant V1 runs on the slab kernels");
   if (o.values < ILU_VALUES_AUTO || o.values > ILU_VALUES_TABULATED) return fail(ILU_EINVAL, "unknown values choice");
   if (o.values == ILU_VALUES_TABULATED && o.precision != ILU_F64)
     return fail(ILU_EINVAL, "tabulated surrogate values are an FP64 option");
@@ -793,6 +801,7 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
 }
 
 ilu_status ilu_destroy(ilu_tet t) {
+  ilu::DeviceRestore keep_device;
   if (!t) return ILU_OK;
   free_device(t);
   delete t;
@@ -815,6 +824,7 @@ ilu_status ilu_export_surrogate(ilu_tet t, double *coefs, size_t n) {
 }
 
 ilu_status ilu_import_surrogate(ilu_tet t, const double *coefs, size_t n) {
+  ilu::DeviceRestore keep_device;
   if (!t || !coefs) return fail(ILU_EINVAL, "null argument");
   if (n != t->host.coefs.size()) return fail(ILU_EINVAL, "coefficient count does not match the handle's degrees");
   for (size_t i = 0; i < n; ++i)
@@ -871,6 +881,7 @@ ilu_status ilu_stencil(ilu_tet t, int x, int y, int z, double out[15]) {
 }
 
 ilu_status ilu_smooth(ilu_tet t, void *x, const void *b, int sweeps, void *stream, double *res_norms) {
+  ilu::DeviceRestore keep_device;
   ilu_status st = check_usable(t);
   if (st != ILU_OK) return st;
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
@@ -895,6 +906,7 @@ ilu_status ilu_smooth(ilu_tet t, void *x, const void *b, int sweeps, void *strea
 }
 
 ilu_status ilu_smooth_host(ilu_tet t, void *x_host, const void *b_host, int sweeps, double *res_norms) {
+  ilu::DeviceRestore keep_device;
   ilu_status st = check_usable(t);
   if (st != ILU_OK) return st;
   if (!x_host || !b_host) return fail(ILU_EINVAL, "null vector");
@@ -916,6 +928,7 @@ ilu_status ilu_smooth_host(ilu_tet t, void *x_host, const void *b_host, int swee
 }
 
 ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double *norm2, void *stream) {
+  ilu::DeviceRestore keep_device;
   ilu_status st = check_usable(t);
   if (st != ILU_OK) return st;
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
@@ -945,6 +958,7 @@ ilu_status ilu_residual(ilu_tet t, const void *x, const void *b, void *r, double
 
 ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
                      int *iters, double *rel_res) {
+  ilu::DeviceRestore keep_device;
   ilu_status st = check_usable(t);
   if (st != ILU_OK) return st;
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
@@ -1033,6 +1047,7 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 }
 
 ilu_status ilu_profile_enable(ilu_tet t, int enable) {
+  ilu::DeviceRestore keep_device;
   if (!t) return fail(ILU_EINVAL, "null handle");
   std::lock_guard<std::mutex> lk(t->mu);
   t->prof = enable != 0;
@@ -1040,6 +1055,7 @@ ilu_status ilu_profile_enable(ilu_tet t, int enable) {
 }
 
 ilu_status ilu_profile_read(ilu_tet t, double ms[3], long long *launches) {
+  ilu::DeviceRestore keep_device;
   if (!t || !ms) return fail(ILU_EINVAL, "null argument");
   std::lock_guard<std::mutex> lk(t->mu);
   ms[0] = ms[1] = ms[2] = 0.0;

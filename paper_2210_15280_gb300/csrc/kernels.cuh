@@ -59,7 +59,8 @@ struct DevTet {
                          // row p at astore[(d < 7 ? d : d - 1) * astride + p], double (float in F32
                          // sweeps); null: assembled on the fly
   int64_t astride;
-  const void *bnd;       // boundary variant V1: 8 values per cell-boundary point (sweep precision), or null
+  const void *bnd;       // boundary variant V1: 8 values per cell-boundary point (sweep precision): its exact
+                         // L^p_d (d in D_l) and 1/D^p; or null
   const int *bnd_off;    // its row offsets (bnd_record in grid.h)
   const double *valsF;   // FP64 sweeps with tabulated surrogate values, 8 per grid point at 8 * index:
   const double *valsB;   // forward L~^p_d (d in D_l) and 0; backward 1/D~^p, L~^{p-d}_d.  Null: the
@@ -159,6 +160,7 @@ struct BandLaunch {
   int ctas;  // total CTAs
   int Z;     // warps (layers) per CTA, 1..8
   int reg;   // row degree held in registers, 0..7 (rstride 4 for <= 3, else 8)
+  bool v1;   // some tet uses boundary variant V1 (its stored factors are consulted)
 };
 size_t band_smem_bytes(int Z);
 cudaError_t launch_band_sub(bool forward, const BandLaunch &L, LaunchStatus *status, long long max_spins,

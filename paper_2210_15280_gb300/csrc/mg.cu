@@ -227,6 +227,7 @@ extern "C" {
 
 ilu_status ilu_mg_setup(const double macro_tet[12], int level, const ilu_coeff *coeff, int poly_degree, int nu,
                         const ilu_opts *opts, ilu_mg *out) {
+  ilu::DeviceRestore keep_device;
   if (!out) return fail(ILU_EINVAL, "null output handle");
   *out = nullptr;
   if (level < 3 || level > 10) return fail(ILU_EINVAL, "multigrid level out of [3, 10]");
@@ -294,6 +295,7 @@ ilu_status ilu_mg_setup(const double macro_tet[12], int level, const ilu_coeff *
 }
 
 ilu_status ilu_mg_destroy(ilu_mg m) {
+  ilu::DeviceRestore keep_device;
   if (!m) return ILU_OK;
   free_mg(m);
   delete m;
@@ -308,6 +310,7 @@ ilu_status ilu_mg_level(ilu_mg m, int level, ilu_tet *out) {
 }
 
 ilu_status ilu_mg_cycle(ilu_mg m, void *x, const void *b, int cycles, void *stream, double *res_norms) {
+  ilu::DeviceRestore keep_device;
   MS(check_mg(m));
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
   if (cycles < 0) return fail(ILU_EINVAL, "negative cycle count");
@@ -329,6 +332,7 @@ ilu_status ilu_mg_cycle(ilu_mg m, void *x, const void *b, int cycles, void *stre
 
 ilu_status ilu_mg_solve(ilu_mg m, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
                         int *iters, double *rel_res) {
+  ilu::DeviceRestore keep_device;
   MS(check_mg(m));
   if (!x || !b) return fail(ILU_EINVAL, "null vector");
   if (method == ILU_MG_VCYCLE) method = ILU_RICHARDSON;
@@ -398,6 +402,7 @@ ilu_status ilu_mg_solve(ilu_mg m, void *x, const void *b, int method, double rto
 }
 
 ilu_status ilu_mg_rate(ilu_mg m, void *e, int steps, void *stream, double *rho, double *history) {
+  ilu::DeviceRestore keep_device;
   MS(check_mg(m));
   if (!e || !rho) return fail(ILU_EINVAL, "null argument");
   if (steps < 1) return fail(ILU_EINVAL, "steps must be positive");

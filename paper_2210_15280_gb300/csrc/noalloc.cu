@@ -19,11 +19,15 @@
 #include <string>
 
 #include "../../include/ilu.h"
+#include "hooks.h"
 #include "kernels.cuh"
 
 namespace ilu {
 // direct view of a handle's device data (defined in capi.cu)
 const DevTet *tet_dev_view(ilu_tet t, int *device, int *precision, size_t *nnodes);
+// refuses null, host-only and failed handles; otherwise holds the handle's lock
+ilu_status tet_acquire(ilu_tet t, std::unique_lock<std::mutex> *lk);
+void tet_mark_failed(ilu_tet t);
 void set_last_error(const std::string &msg);
 }  // namespace ilu
 
@@ -46,6 +50,12 @@ ilu_status fail(ilu_status s, const std::string &msg) {
 extern "C" ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void *b, void *r, double *norm_dev,
                                            void *stream) {
   if (!t || !x || !b || !r || !norm_dev) return fail(ILU_EINVAL, "null argument");
+  ilu::DeviceRestore keep_device;
+  // the same refusals as every other entry point (host-only or failed
+  // handle), and the handle's lock for the launches
+  std::unique_lock<std::mutex> lk;
+  ilu_status st = ilu::tet_acquire(t, &lk);
+  if (st != ILU_OK) return st;
   int device = -1, precision = 0;
   size_t nn = 0;
   const ilu::DevTet *d = ilu::tet_dev_view(t, &device, &precision, &nn);
@@ -62,7 +72,7 @@ extern "C" ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void 
   {
     // first call on this device: look up the array's device address (with
     // the device current); later calls reuse it
-    std::lock_guard<std::mutex> lk(g_mu);
+    std::lock_guard<std::mutex> g(g_mu);
     if (!g_addr[device]) {
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_partials);
@@ -74,12 +84,17 @@ extern "C" ilu_status ilu_residual_noalloc(ilu_tet t, const void *x, const void 
   cudaStream_t s = (cudaStream_t)stream;
   const size_t elem = precision == ILU_F32 ? sizeof(float) : sizeof(double);
   e = cudaMemsetAsync(r, 0, nn * elem, s);  // the kernel writes interior entries only
-  if (e != cudaSuccess) return fail(ILU_ECUDA, std::string("clear r: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    ilu::tet_mark_failed(t);
+    return fail(ILU_ECUDA, std::string("clear r: ") + cudaGetErrorString(e));
+  }
   int used = 0;
   e = ilu::launch_residual(*d, precision == ILU_F32 ? ilu::kSweepF32 : ilu::kSweepF64, x, b, r, partials,
                            kMaxPartials, &used, s);
-  if (e != cudaSuccess) return fail(ILU_ECUDA, std::string("residual launch: ") + cudaGetErrorString(e));
-  e = ilu::launch_norm_finish(partials, used, norm_dev, s);
-  if (e != cudaSuccess) return fail(ILU_ECUDA, std::string("norm launch: ") + cudaGetErrorString(e));
+  if (e == cudaSuccess) e = ilu::launch_norm_finish(partials, used, norm_dev, s);
+  if (e != cudaSuccess) {
+    ilu::tet_mark_failed(t);
+    return fail(ILU_ECUDA, std::string("residual launch: ") + cudaGetErrorString(e));
+  }
   return ILU_OK;
 }

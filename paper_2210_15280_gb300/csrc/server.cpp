@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "../../include/ilu.h"
+#include "hooks.h"
 
 namespace ilu {
 void set_last_error(const std::string &msg);
@@ -369,6 +370,7 @@ void ilu_server_s::slot_main() {
 extern "C" {
 
 ilu_status ilu_server_create(const ilu_server_opts *opts, ilu_server *out) {
+  ilu::DeviceRestore keep_device;
   if (!out) return fail(ILU_EINVAL, "null output handle");
   *out = nullptr;
   if (!opts) return fail(ILU_EINVAL, "null options");
@@ -516,6 +518,7 @@ ilu_status ilu_server_stats(ilu_server s, ilu_stats *st) {
 }
 
 ilu_status ilu_server_destroy(ilu_server s) {
+  ilu::DeviceRestore keep_device;
   if (!s) return ILU_OK;
   {
     std::lock_guard<std::mutex> lk(s->mu);

@@ -485,8 +485,9 @@ static ilu_status factorise(HostTet &t, std::vector<Sample> samples[8], std::str
           t.exactD[i] = Dp;
         }
         if (t.boundary == ILU_BOUNDARY_V1 && on_cell_boundary(N, x, y, z)) {  // records in lexicographic order
+          // V1 (Alg. 1): L^p_d, d in D_l, and the multiplicative inverse of the centre
           for (int d = 0; d < 7; ++d) t.bndL.push_back(Lp[d]);
-          t.bndL.push_back(0.0);
+          t.bndL.push_back(1.0 / Dp);
         }
         for (int f = 0; f < 8; ++f) {
           const int dx = f < 7 ? dir_dx(f) : 0, dy = f < 7 ? dir_dy(f) : 0, dz = f < 7 ? dir_dz(f) : 0;

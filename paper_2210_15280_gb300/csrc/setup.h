@@ -22,7 +22,7 @@ struct HostTet {
   int factor = 0;       // ilu_factor: ILU(0) (Alg. 1) or symmetric Gauss-Seidel
   int boundary = 0;     // ilu_boundary: V2, or V1 with the cell-boundary factors stored
   std::vector<int> bnd_rowoff;  // V1: first record of each interior row (row_id order), then the total
-  std::vector<double> bndL;     // V1: 8 values per cell-boundary point (L^p_d, d in D_l, then 0), lexicographic
+  std::vector<double> bndL;     // V1: 8 values per cell-boundary point (L^p_d, d in D_l, then 1/D^p), lexicographic
   bool const_kappa = true;
   double Kunit[6][4][4] = {};  // unit-coefficient element matrices of the six micro-tet classes
   int off[6][4][3] = {};       // their vertex offsets

@@ -872,6 +872,7 @@ __global__ void __launch_bounds__(REG >= 0 ? 512 : 1024) bwd_wave(const DevTet *
 #pragma unroll
             for (int d = 0; d < 8; ++d) L[d] = Lin[d];
             if (V1 && bndv) {  // L~^{p-d}_d from the stored exact factor where p - d is on the cell boundary
+              if (on_cell_boundary(N, x, y, z)) L[0] = bndv[(size_t)bnd_record(t.bnd_off, N, x, y, z) * 8 + 7];
 #pragma unroll
               for (int d = 0; d < kNumLower; ++d) {
                 const int qx = x - dir_dx(d), qy = y - dir_dy(d), qz = z - dir_dz(d);

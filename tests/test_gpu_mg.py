@@ -173,7 +173,7 @@ def test_v1_vcycle_matches_oracle(g, orc, omg):
         pr = orc.Problem(P, l, orc.Coeff(*co), deg=4)
         m.tet(l).import_surrogate(pr.coefs)
         Ls, Dinv = pr.surrogate_factors()
-        fac[l] = (orc.v1_factors(pr.N, Ls, pr.L), Dinv)
+        fac[l] = orc.v1_factors(pr.N, Ls, Dinv, pr.L, pr.D)
     H = omg.Hierarchy(P, level, coeff=orc.Coeff(*co), nu=3, factors=fac)
     x = si.boundary_data(level, 56)
     b = si.rhs(level, 57)

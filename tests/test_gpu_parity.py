@@ -118,11 +118,10 @@ def test_slab_partition_is_bitwise_invariant(g, orc, prec, kernel):
 
 
 def test_band_kernels_at_full_bench_level(g, orc):
-    """Level 9 (the size where the band kernels are chosen): sampled points of
-    one MIXED sweep from x = 0 against the oracle's local definition: with
-    x = C~^{-1} r, the point's residual equation of C~ holds (checked through
-    the oracle's factors at a handful of rows) -- the full oracle sweep is
-    too slow at this size, so compare the sweep's effect on the residual."""
+    """Level 9 (the size where the band kernels are chosen): four MIXED sweeps
+    from x = 0 contract and stay finite, and the slab kernels give the same
+    iterate to the FP32 bar.  The oracle check of the same sweeps is
+    test_level9_sweep_solves_the_oracle_residual_equation."""
     level, deg = 9, 6
     P = si.macro_tet(5)
     t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=deg, precision=g.MIXED)
@@ -140,6 +139,63 @@ def test_band_kernels_at_full_bench_level(g, orc):
     x2 = torch.zeros_like(b)
     t2.smooth(x2, b, 4)
     assert rel(x.cpu().numpy(), x2.cpu().numpy()) < 1e-5
+
+
+def level9_sample_points(N, seed, n_random=240):
+    """Interior points for the level-9 checks: seeded random points plus
+    points on each face of the interior, its edges and corners."""
+    u = si.uniform(seed, 3 * n_random)
+    pts = set()
+    for k in range(n_random):
+        z = 1 + int(u[3 * k + 2] * (N - 3))
+        y = 1 + int(u[3 * k + 1] * (N - 2 - z))
+        x = 1 + int(u[3 * k] * (N - 1 - y - z))
+        pts.add((x, y, z))
+    for m in (1, 2, 17, N // 3, N - 5):
+        for a, c in ((1, m), (m, 1), (2, m)):
+            pts.update({(1, a, c), (a, 1, c), (a, c, 1)})
+            if a + c <= N - 2:
+                pts.add((N - 1 - a - c, a, c))
+    pts.update({(1, 1, 1), (N - 3, 1, 1), (1, N - 3, 1), (1, 1, N - 3)})
+    return sorted(p for p in pts if p[0] >= 1 and p[1] >= 1 and p[2] >= 1 and sum(p) <= N - 1)
+
+
+@pytest.mark.parametrize("prec,kernel,tol", [("MIXED", "BAND", 1e-5), ("F32", "BAND", 1e-5), ("MIXED", "SLAB", 1e-5),
+                                             ("F64", "AUTO", 1e-12)])
+def test_level9_sweep_solves_the_oracle_residual_equation(g, orc, prec, kernel, tol):
+    """Level 9, the bench's single-tet size, element by element at sampled
+    points: one sweep from x0 (Dirichlet data, interior 0) gives w = x1 - x0
+    = C~^-1 r.  At each sampled point the oracle evaluates the library's
+    exported surrogate polynomials (direct tensor evaluation) on the point's
+    neighbourhood and forms (L~ D~ L~^T w)_p, and computes r_p from its own
+    element-assembled stencil; the two agree to the precision's bar."""
+    level, deg = 9, 6
+    P = si.macro_tet(5)
+    p = getattr(g, prec)
+    dt = torch.float32 if p == g.F32 else torch.float64
+    t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=deg, precision=p,
+              kernel=getattr(g, "KERNEL_" + kernel))
+    N = t.N
+    coefs = t.export_surrogate().reshape(8, -1)
+    ids, _ = orc.interior_ids(N)
+    npdt = np.float32 if p == g.F32 else np.float64
+    x0 = si.boundary_data(level, 11).astype(npdt).astype(np.float64)
+    x0[ids >= 0] = 0.0
+    b = si.rhs(level, 12).astype(npdt).astype(np.float64)
+    x = dev(x0, dt)
+    t.smooth(x, dev(b, dt), 1)
+    w = x.cpu().numpy().astype(np.float64) - x0
+    del x
+    at = lambda v: (lambda q: v[orc.index(N, *q)])
+    co = orc.Coeff("const")
+    cache = {}
+    lhs, rhs = [], []
+    for q in level9_sample_points(N, 13):
+        lhs.append(orc.ldlt_apply_at(N, [deg] * 3, coefs, at(w), q, cache))
+        rhs.append(orc.local_residual(P, N, co, at(x0), at(b), q))
+    lhs, rhs = np.array(lhs), np.array(rhs)
+    assert len(rhs) > 250
+    assert np.abs(lhs - rhs).max() <= tol * np.abs(rhs).max()
 
 
 @pytest.mark.parametrize("prec", ["F64", "MIXED", "F32"])
@@ -277,21 +333,25 @@ def test_tabulated_values_bitwise_equal_on_the_fly(g, level, kind, deg, boundary
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
 
 
-@pytest.mark.parametrize("level,kind,prec", [(3, "const", "F64"), (4, "sinprod", "F64"), (5, "kappa_i", "F64"),
-                                             (6, "sinprod", "F64"), (5, "sinprod", "MIXED"), (7, "const", "MIXED"),
-                                             (6, "kappa_i", "F32")])
-def test_v1_boundary_variant_matches_oracle(g, orc, level, kind, prec):
-    """Variant V1: exact factors at the cell-boundary points, surrogates
-    elsewhere (the oracle's v1_factors), through the slab kernels."""
+@pytest.mark.parametrize("level,kind,prec,kernel", [
+    (3, "const", "F64", "SLAB"), (4, "sinprod", "F64", "SLAB"), (5, "kappa_i", "F64", "SLAB"),
+    (6, "sinprod", "F64", "SLAB"), (5, "sinprod", "MIXED", "SLAB"), (7, "const", "MIXED", "SLAB"),
+    (6, "kappa_i", "F32", "SLAB"), (5, "sinprod", "MIXED", "BAND"), (7, "const", "MIXED", "BAND"),
+    (6, "kappa_i", "F32", "BAND")])
+def test_v1_boundary_variant_matches_oracle(g, orc, level, kind, prec, kernel):
+    """Variant V1: the stored exact factors (L^p_d and 1/D^p) at the
+    cell-boundary points, surrogates elsewhere (the oracle's v1_factors)."""
     P, co, pr = problem(orc, level, 80 + level, kind, 4)
     p = getattr(g, prec)
     dt = torch.float32 if p == g.F32 else torch.float64
-    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=4, precision=p, boundary=g.BOUNDARY_V1)
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=4, precision=p, boundary=g.BOUNDARY_V1,
+              kernel=getattr(g, "KERNEL_" + kernel))
     t.import_surrogate(pr.coefs)
     x0 = si.boundary_data(level, 81)
     b = si.rhs(level, 82)
     Ls, Dinv = pr.surrogate_factors()
-    xo = orc.smooth(pr.A, pr.N, orc.v1_factors(pr.N, Ls, pr.L), Dinv, x0.copy(), b, 2)
+    L1, D1 = orc.v1_factors(pr.N, Ls, Dinv, pr.L, pr.D)
+    xo = orc.smooth(pr.A, pr.N, L1, D1, x0.copy(), b, 2)
     xd = dev(x0, dt)
     t.smooth(xd, dev(b, dt), 2)
     assert rel(xd.cpu().numpy().astype(np.float64), xo) < (1e-12 if p == g.F64 else 2e-5)

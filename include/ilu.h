@@ -162,17 +162,23 @@ typedef enum { ILU_VALUES_AUTO = 0, ILU_VALUES_ON_THE_FLY = 1, ILU_VALUES_TABULA
  * Sampling, fit, tables and sweeps are the same for both. */
 typedef enum { ILU_FACTOR_ILU0 = 0, ILU_FACTOR_SGS = 1 } ilu_factor;
 
-/* Substitution kernels of the FP32/MIXED sweeps.  Both run the same
- * arithmetic (Alg. 2, V2) and agree to rounding; they differ in how the
+/* Substitution kernels of the FP32/MIXED sweeps.  All run the same
+ * arithmetic (Alg. 2) and agree to rounding; they differ in how the
  * hyperplane wavefront is mapped onto the GPU:
- *   ILU_KERNEL_SLAB  a CTA per z-slab advancing one hyperplane per step with
- *                    block-wide synchronisation (faster up to level 8);
- *   ILU_KERNEL_BAND  a warp per (layer, 32-row band) advancing one row point
- *                    per lane and step, synchronised point to point through
- *                    tagged words (faster from level 9 on).
- * ILU_KERNEL_AUTO picks by level.  F64 sweeps and degrees above 7 always use
- * the slab kernels. */
-typedef enum { ILU_KERNEL_AUTO = 0, ILU_KERNEL_SLAB = 1, ILU_KERNEL_BAND = 2 } ilu_kernel;
+ *   ILU_KERNEL_SLAB    a CTA per z-slab advancing one hyperplane per step with
+ *                      block-wide synchronisation, slabs of a tet as clusters;
+ *   ILU_KERNEL_BAND    a warp per (layer, 32-row band) advancing one row point
+ *                      per lane and step, synchronised point to point through
+ *                      tagged words (fastest from level 9 on);
+ *   ILU_KERNEL_PACKED  one CTA per tet: its rows packed onto 384 lanes by a
+ *                      host-computed schedule, one point per lane and step,
+ *                      the CTA meeting at a block barrier after each step; no
+ *                      CTA waits on another (levels up to 8, row degrees up to
+ *                      6; fastest up to level 6, and the kernels to set up
+ *                      tets with for batch throughput).
+ * ILU_KERNEL_AUTO picks by level: packed up to 6, slab for 7 and 8, band from
+ * 9.  F64 sweeps and degrees above 7 always use the slab kernels. */
+typedef enum { ILU_KERNEL_AUTO = 0, ILU_KERNEL_SLAB = 1, ILU_KERNEL_BAND = 2, ILU_KERNEL_PACKED = 3 } ilu_kernel;
 
 typedef struct ilu_tet_s *ilu_tet;
 typedef struct ilu_batch_s *ilu_batch;
@@ -305,15 +311,61 @@ typedef enum { ILU_RICHARDSON = 0, ILU_PCG = 1, ILU_MG_VCYCLE = 2, ILU_MG_PCG = 
 ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol, int max_iter, void *stream,
                      int *iters, double *rel_res);
 
+/* The row schedule the packed kernels (ILU_KERNEL_PACKED) follow for one
+ * substitution at a level (the same for every tet of that level), for
+ * inspection and testing.  lanes: 0 for the kernels' own lane count, else
+ * 1..511 for the same construction on that many lanes.  *nsteps and
+ * *lanes_out receive its size; with entries (8 ints per interior row: step of
+ * its first point, n | y << 10 | z << 20 with n its point count, grid index
+ * of its point x = 0, row id, three producer codes, 0) and lane_off (lanes +
+ * 1 ints) non-null they receive the schedule, rows grouped by lane in step
+ * order.  A producer code has its mode in bits 30-31: 0 no such interior row;
+ * 1 ring: the producer's lane in bits 0-8 and, in bits 9-13, the step
+ * distance k0 of the first value the consumer reads; 2 global: bits 0-29 the
+ * grid index of the producer row's point x = 0.  Forward producers of row
+ * (y, z): (y-1, z), (y, z-1), (y+1, z-1); backward: (y+1, z), (y, z+1),
+ * (y-1, z+1).  Host-only; the paper sweeps lexicographically on one core,
+ * this arrangement is the library's.  ILU_EINVAL for a level outside 2..8. */
+ilu_status ilu_packed_schedule(int level, int forward, int lanes, int *nsteps, int *lanes_out, int *entries,
+                               int *lane_off);
+
+/* Split n macro-tetrahedra over nranks GPUs for a batch or a request stream
+ * on several devices: cost[i] (host, finite, >= 0; e.g. interior points x
+ * sweeps) is tet i's work, rank_of[i] (host) receives its GPU.  Longest
+ * processing time first: tets by decreasing cost, each to the least loaded
+ * rank so far (ties to the lower rank, equal costs in index order); the
+ * largest load stays within 4/3 of the optimum.  load (host, nullable,
+ * nranks) receives each rank's total.  Interior solves on different tets are
+ * independent (Sec. 2.1: the interface data are read, never written), so the
+ * shards need no exchange.  Host-only; the paper runs one macro-primitive per
+ * process, the split is this library's.  ILU_EINVAL for n < 0, nranks < 1,
+ * null arrays or a bad cost. */
+ilu_status ilu_partition(int n, const double *cost, int nranks, int *rank_of, double *load);
+
+/* The dependency-depth floor of a substitution step on this GPU, for
+ * roofline reporting: one CTA of `threads` threads (a multiple of 32, up to
+ * 1024) runs `steps` steps of the shortest body a wavefront step can have --
+ * three neighbour values from a shared-memory ring, seven dependent FMAs, the
+ * result written back, a block barrier -- and *cycles_per_step receives the
+ * SM cycles per step (best of two timed runs).  Alg. 2's substitutions are
+ * chains of 3N - 11 such hyperplane steps (Sec. 2.1); steps x this floor
+ * bounds any schedule that synchronises by block barrier.  ILU_ENODEV
+ * without that device.  The paper has no counterpart. */
+ilu_status ilu_step_floor(int device, int threads, int steps, double *cycles_per_step);
+
 /* ----------------------------------------------------------------- batch -- */
 
 /* Group tets for smoothing together.  All tets must live on one device and
- * share one precision; levels and degrees may differ.  opts (nullable) may set
- * max_wait_spins and slabs: > 0 fixes the wavefront partition of every tet
- * (as in ilu_setup); otherwise the batch autotunes it, timing one pass of
- * the batch for each candidate (layers per slab CTA 1, 2, 4 x cluster size
- * for most resident CTAs or largest) on scratch vectors and keeping the
- * fastest.  Batches use the slab substitution kernels.  The batch
+ * share one precision; levels and degrees may differ.  Each tet runs on the
+ * substitution kernels its own handle uses, so that it gets its single-tet
+ * sweep bit for bit: tets on the packed kernels (the FP32/MIXED default up to
+ * level 8) in one launch per row-table layout, a CTA per tet, most steps
+ * first; the others on the slab kernels, grouped by level.  opts (nullable)
+ * may set max_wait_spins and slabs: > 0 fixes the slab partition of every
+ * slab tet (as in ilu_setup); otherwise the batch autotunes it, timing one
+ * pass of the batch for each candidate (layers per slab CTA 1, 2, 4 x cluster
+ * size for most resident CTAs or largest) on scratch vectors and keeping the
+ * fastest.  The batch
  * keeps references to the tets, which must outlive it; it reuses each tet's
  * scratch, so a tet must not be smoothed by another call while a batch call
  * on it runs.  ILU_EINVAL for an empty batch, a null or failed tet, or mixed

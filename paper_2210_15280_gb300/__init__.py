@@ -20,7 +20,7 @@ ILU_OK, ILU_EINVAL, ILU_ENOMEM, ILU_ECUDA, ILU_ESINGULAR, ILU_ENOTCONV, ILU_ETIM
 F64, F32, MIXED = 0, 1, 2
 COEFF_CONST, COEFF_SINPROD, COEFF_KAPPA_I = 0, 1, 2
 RICHARDSON, PCG, MG_VCYCLE, MG_PCG = 0, 1, 2, 3
-KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND = 0, 1, 2
+KERNEL_AUTO, KERNEL_SLAB, KERNEL_BAND, KERNEL_PACKED = 0, 1, 2, 3
 FACTOR_ILU0, FACTOR_SGS = 0, 1
 STENCIL_AUTO, STENCIL_ON_THE_FLY, STENCIL_STORED = 0, 1, 2
 VALUES_AUTO, VALUES_ON_THE_FLY, VALUES_TABULATED = 0, 1, 2
@@ -38,7 +38,7 @@ EXPORTS = [
     "ilu_server_stats", "ilu_server_destroy", "ilu_num_nodes", "ilu_num_interior", "ilu_index",
     "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read", "ilu_residual_noalloc",
     "ilu_mg_setup", "ilu_mg_destroy", "ilu_mg_level", "ilu_mg_cycle", "ilu_mg_solve", "ilu_mg_rate",
-    "ilu_lfa_order", "ilu_vertex_order",
+    "ilu_lfa_order", "ilu_vertex_order", "ilu_packed_schedule", "ilu_partition", "ilu_step_floor",
 ]
 
 
@@ -131,6 +131,9 @@ def lib():
         L.ilu_profile_enable.argtypes = [vp, i]
         L.ilu_profile_read.argtypes = [vp, vp, P(ctypes.c_longlong)]
         L.ilu_num_nodes.argtypes = [i]; L.ilu_num_nodes.restype = sz
+        L.ilu_packed_schedule.argtypes = [i, i, i, vp, vp, vp, vp]
+        L.ilu_partition.argtypes = [i, vp, i, vp, vp]
+        L.ilu_step_floor.argtypes = [i, i, i, vp]
         L.ilu_num_interior.argtypes = [i]; L.ilu_num_interior.restype = sz
         L.ilu_index.argtypes = [i, i, i, i]; L.ilu_index.restype = ctypes.c_longlong
         L.ilu_last_error.restype = ctypes.c_char_p
@@ -147,6 +150,39 @@ def lib():
 def _check(st):
     if st != ILU_OK:
         raise IluError(st, lib().ilu_last_error().decode(errors="replace"))
+
+
+def step_floor(threads=384, steps=4096, device=0):
+    """SM cycles per step of the shortest barrier-synchronised substitution
+    step (ilu_step_floor)."""
+    c = ctypes.c_double(0.0)
+    _check(lib().ilu_step_floor(int(device), int(threads), int(steps), ctypes.byref(c)))
+    return c.value
+
+
+def partition(costs, nranks):
+    """Split tets of the given costs over nranks GPUs (ilu_partition, longest
+    processing time first): (rank of each tet, load of each rank)."""
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    rank_of = np.zeros(len(c), dtype=np.int32)
+    load = np.zeros(int(nranks))
+    _check(lib().ilu_partition(len(c), _ptr(c), int(nranks), _ptr(rank_of), _ptr(load)))
+    return rank_of, load
+
+
+def packed_schedule(level, forward=True, lanes=0):
+    """Row schedule of the packed kernels for one substitution at `level`
+    (ilu_packed_schedule): (nsteps, lanes, entries[rows, 8], lane_off)."""
+    ns, ln = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), ctypes.byref(ns), ctypes.byref(ln),
+                                     None, None))
+    n = 2 ** int(level)
+    rows = (n - 3) * (n - 2) // 2 if n >= 4 else 0
+    ent = np.zeros((rows, 8), dtype=np.int32)
+    off = np.zeros(ln.value + 1, dtype=np.int32)
+    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), ctypes.byref(ns), ctypes.byref(ln),
+                                     _ptr(ent), _ptr(off)))
+    return ns.value, ln.value, ent, off
 
 
 def num_nodes(level):

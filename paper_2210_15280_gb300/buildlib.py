@@ -12,8 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libilu.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "wavefront.cu", "band.cu", "capi.cu", "noalloc.cu", "batch.cu", "mg.cu", "setup.cpp", "lfa.cpp",
-           "server.cpp"]
+SOURCES = ["kernels.cu", "wavefront.cu", "band.cu", "packed.cu", "packed_plan.cpp", "capi.cu", "noalloc.cu", "batch.cu", "mg.cu", "setup.cpp", "lfa.cpp",
+           "server.cpp", "shard.cpp", "floor.cu"]
 
 
 def _nvcc():

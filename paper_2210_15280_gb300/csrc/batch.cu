@@ -3,15 +3,23 @@
 // A pass over the batch (one sweep of Alg. 2 on every tet) is
 //   1. one reset of all progress words and ticket counters,
 //   2. one residual launch covering every tet (1-D grid, per-tet block ranges),
-//   3. per group of tets with the same level and row-polynomial layout, one
-//      forward and one backward wavefront launch; the groups are independent
-//      branches of the pass, so their kernels run concurrently.
-// Inside a group the clusters of every tet take tickets tet by tet, in
-// dependency order within a tet, so any cluster waits only on clusters that
-// took earlier tickets and are therefore resident or finished: the launch
-// cannot deadlock whatever the residency.  A tet whose row degree is below
-// its group's register degree evaluates zero leading coefficients, which
-// leaves its results bit for bit those of its own launch.
+//   3. the substitutions, as independent branches of the pass so that their
+//      kernels run concurrently:
+//      - tets whose handles use the packed kernels: one launch per row-table
+//        layout, a CTA per tet holding its forward and backward substitution,
+//        tets ordered by their step count, longest first (the CTAs of the
+//        longest tets start first, the short ones fill in behind them); no
+//        CTA waits on another;
+//      - the other tets, grouped by level and row-polynomial layout: one
+//        forward and one backward slab launch per group.  Inside a group the
+//        clusters of every tet take tickets tet by tet, in dependency order
+//        within a tet, so any cluster waits only on clusters that took earlier
+//        tickets and are therefore resident or finished: the launch cannot
+//        deadlock whatever the residency.
+// A tet whose row degree is below its launch's register degree evaluates
+// zero leading coefficients, which leaves its results bit for bit those of
+// its own launch.  The autotuner times the slab partitions (packed tets have
+// no partition to choose).
 //
 // The passes of one ilu_batch_smooth call are captured once into a CUDA graph
 // (re-captured when `sweeps` changes) and replayed on the caller's stream.
@@ -61,6 +69,17 @@ struct Group {
   cudaEvent_t done = nullptr;
 };
 
+// Tets on the packed kernels with the same row-table layout: one launch, a
+// CTA per tet, longest tets first (their CTAs start first).
+struct PackedGroup {
+  int dxp = 0, reg = 0;
+  bool v1 = false;
+  std::vector<int> members;  // tet indices, most steps first
+  PackedLaunch pl = {};
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
 }  // namespace
 
 struct ilu_batch_s {
@@ -71,6 +90,11 @@ struct ilu_batch_s {
   std::vector<TetView> views;
   std::vector<DevTet> dev;  // host copies of d_tets
   std::vector<Group> groups;
+  std::vector<PackedGroup> pgroups;
+  int *d_porder = nullptr;  // tet order of the packed launches
+  int *d_rlists = nullptr;  // per operator kind: tet order, then block prefix (residual launches)
+  int rn[3] = {0, 0, 0}, rblocks[3] = {0, 0, 0};
+  size_t rat[3] = {0, 0, 0};
   int total_blocks = 0, nflags = 0;
   DevTet *d_tets = nullptr;
   int *d_bprefix = nullptr, *d_maps = nullptr, *d_flags = nullptr;
@@ -100,6 +124,15 @@ void free_plan(ilu_batch b) {
     if (g.done) cudaEventDestroy(g.done);
   }
   b->groups.clear();
+  for (auto &g : b->pgroups) {
+    if (g.st) cudaStreamDestroy(g.st);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  b->pgroups.clear();
+  cudaFree(b->d_porder);
+  b->d_porder = nullptr;
+  cudaFree(b->d_rlists);
+  b->d_rlists = nullptr;
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->ptr_ev) cudaEventDestroy(b->ptr_ev);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -137,8 +170,13 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   // rows in registers, rows in shared memory, tabulated values
   auto cls = [](const TetView &v) { return v.reg >= 0 ? 1 : (v.reg == kWaveTabulated ? 2 : 0); };
   std::map<std::tuple<int, int, int>, int> key;
+  std::map<int, int> pkey;  // packed tets by table layout
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
+    if (v.packed) {
+      pkey.emplace(v.rstride, 0);
+      continue;
+    }
     const auto k = std::make_tuple(-v.N, cls(v), v.rstride);  // largest levels first
     auto it = key.find(k);
     if (it == key.end()) {
@@ -149,8 +187,19 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   int gi = 0;
   for (auto &kv : key) kv.second = gi++;
   b->groups.assign(key.size(), Group{});
+  int pgi = 0;
+  for (auto &kv : pkey) kv.second = pgi++;
+  b->pgroups.assign(pkey.size(), PackedGroup{});
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
+    if (v.packed) {
+      PackedGroup &pg = b->pgroups[pkey[v.rstride]];
+      pg.dxp = v.rstride;
+      pg.reg = v.dx <= 3 ? 3 : 6;  // the degree of the tets' packed tables (zero padded, as their own launches)
+      pg.v1 = pg.v1 || v.dev->bnd != nullptr;
+      pg.members.push_back(i);
+      continue;
+    }
     Group &g = b->groups[key[std::make_tuple(-v.N, cls(v), v.rstride)]];
     g.N = v.N;
     g.dxp = v.rstride;
@@ -159,6 +208,15 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   }
   // per-tet descriptors with geometry and progress words in the batch's flag array
   b->dev.resize(n);
+  for (auto &pg : b->pgroups) {
+    for (int i : pg.members) {
+      DevTet d = *b->views[i].dev;
+      d.fwd.P = d.bwd.P = 0;  // no slab launches, no progress words
+      b->dev[i] = d;
+    }
+    std::stable_sort(pg.members.begin(), pg.members.end(),
+                     [&](int a, int c) { return b->views[a].packed_steps > b->views[c].packed_steps; });
+  }
   int off = 0;
   for (auto &g : b->groups) {
     for (int i : g.members) {
@@ -188,6 +246,24 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   BK(cudaMemcpy(b->d_tets, b->dev.data(), sizeof(DevTet) * n, cudaMemcpyHostToDevice), "upload tets");
   BK(cudaMalloc(&b->d_bprefix, sizeof(int) * (n + 1)), "cudaMalloc block prefix");
   BK(cudaMemcpy(b->d_bprefix, bprefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "upload prefix");
+  {  // residual launches by operator kind: per kind the tets and their block prefix
+    std::vector<int> lists;
+    for (int op = 0; op < 3; ++op) {
+      std::vector<int> ids;
+      for (int i = 0; i < n; ++i)
+        if (residual_op(b->dev[i]) == op) ids.push_back(i);
+      b->rn[op] = (int)ids.size();
+      b->rat[op] = lists.size();
+      lists.insert(lists.end(), ids.begin(), ids.end());
+      int acc = 0;
+      lists.push_back(0);
+      for (int i : ids) lists.push_back(acc += residual_blocks(b->views[i].N));
+      b->rblocks[op] = acc;
+    }
+    BK(cudaMalloc(&b->d_rlists, sizeof(int) * lists.size()), "cudaMalloc residual lists");
+    BK(cudaMemcpy(b->d_rlists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice),
+       "upload residual lists");
+  }
   BK(cudaMalloc(&b->d_ptrs, sizeof(void *) * 2 * n), "cudaMalloc pointer arrays");
   BK(cudaMemset(b->d_ptrs, 0, sizeof(void *) * 2 * n), "cudaMemset pointer arrays");
   BK(cudaMallocHost(&b->h_ptrs, sizeof(void *) * 2 * n), "cudaMallocHost pointer arrays");
@@ -245,8 +321,29 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     for (int i : G.members) maps.push_back(i);
     (void)m;
   }
-  BK(cudaMalloc(&b->d_maps, sizeof(int) * maps.size()), "cudaMalloc cluster maps");
-  BK(cudaMemcpy(b->d_maps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice), "upload cluster maps");
+  BK(cudaMalloc(&b->d_maps, sizeof(int) * std::max<size_t>(maps.size(), 1)), "cudaMalloc cluster maps");
+  if (!maps.empty())
+    BK(cudaMemcpy(b->d_maps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice), "upload cluster maps");
+  {
+    std::vector<int> porder;
+    for (auto &pg : b->pgroups) porder.insert(porder.end(), pg.members.begin(), pg.members.end());
+    BK(cudaMalloc(&b->d_porder, sizeof(int) * std::max<size_t>(porder.size(), 1)), "cudaMalloc packed order");
+    if (!porder.empty())
+      BK(cudaMemcpy(b->d_porder, porder.data(), sizeof(int) * porder.size(), cudaMemcpyHostToDevice),
+         "upload packed order");
+    size_t at = 0;
+    for (auto &pg : b->pgroups) {
+      PackedLaunch &L = pg.pl;
+      L.tets = b->d_tets;
+      L.order = b->d_porder + at;
+      L.ntets = (int)pg.members.size();
+      L.reg = pg.reg;
+      L.v1 = pg.v1;
+      at += pg.members.size();
+      BK(cudaStreamCreateWithFlags(&pg.st, cudaStreamNonBlocking), "cudaStreamCreate");
+      BK(cudaEventCreateWithFlags(&pg.done, cudaEventDisableTiming), "cudaEventCreate");
+    }
+  }
   for (size_t g = 0; g < b->groups.size(); ++g) {
     Group &G = b->groups[g];
     const int m = (int)G.members.size();
@@ -267,10 +364,19 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
   cudaStream_t s = b->cap;
   for (int k = 0; k < sweeps; ++k) {
     BK(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * b->nflags, s), "reset flags");
-    BK(launch_residual_batch(b->d_tets, b->d_bprefix, b->n, b->total_blocks, b->kind, b->d_ptrs,
-                             b->d_ptrs + b->n, s),
-       "batched residual launch");
+    for (int op = 0; op < 3; ++op) {
+      const int *order = b->d_rlists + b->rat[op];
+      BK(launch_residual_batch(b->d_tets, order, order + b->rn[op], b->rn[op], b->rblocks[op], b->kind, op,
+                               b->d_ptrs, b->d_ptrs + b->n, s),
+         "batched residual launch");
+    }
     BK(cudaEventRecord(b->fork, s), "fork");
+    for (auto &g : b->pgroups) {  // first: the packed launches hold the longest tets
+      BK(cudaStreamWaitEvent(g.st, b->fork, 0), "fork wait");
+      BK(launch_packed(g.pl, g.st), "packed substitution launch");
+      BK(cudaEventRecord(g.done, g.st), "join");
+      BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
+    }
     for (auto &g : b->groups) {
       BK(cudaStreamWaitEvent(g.st, b->fork, 0), "fork wait");
       BK(launch_forward(g.wl, b->d_status, b->max_spins, g.st), "forward launch");
@@ -278,6 +384,10 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
       BK(cudaEventRecord(g.done, g.st), "join");
       BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
     }
+    if (!b->pgroups.empty())  // x += the packed tets' results (the slab tets updated x themselves)
+      BK(launch_packed_io(0, b->kind == kSweepMixed, b->d_tets, b->d_bprefix, b->n, b->total_blocks, b->d_ptrs,
+                          nullptr, s),
+         "packed update launch");
   }
   return ILU_OK;
 }
@@ -314,6 +424,9 @@ double time_pass(ilu_batch b, void *scratch) {
 
 // Autotuner: layers per slab CTA x cluster policy, timed on the batch itself.
 ilu_status tune(ilu_batch b) {
+  bool slab = false;
+  for (const auto &v : b->views) slab = slab || !v.packed;
+  if (!slab) return build(b, 0, false);  // packed tets only: nothing to tune
   size_t nmax = 0;
   for (const auto &v : b->views) nmax = std::max(nmax, v.nnodes);
   void *scratch = nullptr;

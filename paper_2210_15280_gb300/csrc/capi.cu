@@ -19,6 +19,7 @@
 #include "../../include/ilu.h"
 #include "hooks.h"
 #include "kernels.cuh"
+#include "packed.h"
 #include "setup.h"
 
 using namespace ilu;
@@ -74,6 +75,12 @@ struct ilu_tet_s {
   void *d_bw = nullptr;
   unsigned long long *d_bstreams = nullptr;
   BandLaunch bl = {};
+  // packed substitutions (packed.cu): schedules of both directions
+  bool use_packed = false;
+  void *d_pkF = nullptr, *d_pkB = nullptr;  // compact row polynomials of the packed kernels
+  int4 *d_pk = nullptr;      // schedules, lane offsets and row map in one block
+  float *d_pkw = nullptr;    // the packed array [T][kPackedLanes]
+  PackedLaunch pl = {};
   const int *band_tprefix = nullptr;
   int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
   int *d_chunks = nullptr;  // residual work list (32-point row chunks)
@@ -115,6 +122,10 @@ void free_device(ilu_tet t) {
   t->ev_pool.clear();
   cudaFree(t->d_tabF); cudaFree(t->d_tabB); cudaFree(t->d_w); cudaFree(t->d_kappa); cudaFree(t->d_astore);
   cudaFree(t->d_bnd); cudaFree(t->d_bnd_off);
+  cudaFree(t->d_pk); cudaFree(t->d_pkw); cudaFree(t->d_pkF); cudaFree(t->d_pkB);
+  t->d_pk = nullptr;
+  t->d_pkw = nullptr;
+  t->d_pkF = t->d_pkB = nullptr;
   cudaFree(t->d_valsF); cudaFree(t->d_valsB);
   t->d_valsF = t->d_valsB = nullptr;
   t->d_astore = nullptr;
@@ -299,6 +310,79 @@ ilu_status upload_band(ilu_tet t, int requested_slabs) {
   return ILU_OK;
 }
 
+// The FP32 row tables ([row][pair p][k][2], k padded to rstride) rearranged
+// for the packed kernels: [row][k][pair p][2], 32 bytes per k, with
+// packed_degree(dx) + 1 coefficients (zero padded), the degree the kernels
+// are instantiated for: every tet of a row-table class shares one launch.
+int packed_degree(int dx) { return dx <= 3 ? 3 : kPackedMaxDegree; }
+void compact_rows(const HostTet &h, const std::vector<float> &tab, std::vector<float> &out) {
+  const int64_t R = num_rows(h.N);
+  const int S = h.rstride, K = packed_degree(h.dx) + 1;
+  out.assign((size_t)R * K * 8, 0.0f);
+  for (int64_t r = 0; r < R; ++r)
+    for (int k = 0; k < K; ++k)
+      for (int p = 0; p < 4; ++p)
+        for (int j = 0; j < 2; ++j)
+          out[(((size_t)r * K + k) * 4 + p) * 2 + j] = k < S ? tab[(((size_t)r * 4 + p) * S + k) * 2 + j] : 0.0f;
+}
+
+ilu_status upload_packed_tables(ilu_tet t) {
+  const HostTet &h = t->host;
+  std::vector<float> cf, cb;
+  compact_rows(h, h.tabF32, cf);
+  compact_rows(h, h.tabB32, cb);
+  if (!t->d_pkF) CK(cudaMalloc(&t->d_pkF, sizeof(float) * std::max<size_t>(cf.size(), 4)), "cudaMalloc packed tables");
+  if (!t->d_pkB) CK(cudaMalloc(&t->d_pkB, sizeof(float) * std::max<size_t>(cb.size(), 4)), "cudaMalloc packed tables");
+  if (!cf.empty()) CK(cudaMemcpy(t->d_pkF, cf.data(), sizeof(float) * cf.size(), cudaMemcpyHostToDevice), "upload packed tables");
+  if (!cb.empty()) CK(cudaMemcpy(t->d_pkB, cb.data(), sizeof(float) * cb.size(), cudaMemcpyHostToDevice), "upload packed tables");
+  t->dev.pkF = t->d_pkF;
+  t->dev.pkB = t->d_pkB;
+  return ILU_OK;
+}
+
+ilu_status upload_packed(ilu_tet t) {
+  {
+    ilu_status ts = upload_packed_tables(t);
+    if (ts != ILU_OK) return ts;
+  }
+  const int N = t->host.N;
+  std::string err;
+  const PackedPlan *pl = packed_plan_cached(N, &err);
+  if (!pl) return fail(ILU_EINVAL, err);
+  const size_t ne = pl->fwd.size();
+  const int lanes = pl->lanes;
+  static_assert(sizeof(PackedEntry) == 2 * sizeof(int4), "a schedule entry is two int4");
+  // one block: forward entries, backward entries, lane offsets, row map
+  const size_t ints = 16 * ne + (lanes + 1) + pl->row_map.size();
+  std::vector<int> blob(std::max<size_t>(ints, 4), 0);
+  if (ne) {
+    std::memcpy(blob.data(), pl->fwd.data(), sizeof(PackedEntry) * ne);
+    std::memcpy(blob.data() + 8 * ne, pl->bwd.data(), sizeof(PackedEntry) * ne);
+  }
+  std::memcpy(blob.data() + 16 * ne, pl->lane_off.data(), sizeof(int) * (lanes + 1));
+  if (!pl->row_map.empty())
+    std::memcpy(blob.data() + 16 * ne + lanes + 1, pl->row_map.data(), sizeof(int) * pl->row_map.size());
+  CK(cudaMalloc(&t->d_pk, sizeof(int) * blob.size()), "cudaMalloc packed schedule");
+  CK(cudaMemcpy(t->d_pk, blob.data(), sizeof(int) * blob.size(), cudaMemcpyHostToDevice), "upload packed schedule");
+  CK(cudaMalloc(&t->d_pkw, sizeof(float) * (size_t)pl->nsteps * lanes), "cudaMalloc packed array");
+  CK(cudaMemset(t->d_pkw, 0, sizeof(float) * (size_t)pl->nsteps * lanes), "cudaMemset packed array");
+  const int *base = reinterpret_cast<const int *>(t->d_pk);
+  PackedDev &p = t->dev.pk;
+  p.ent_f = t->d_pk;
+  p.ent_b = t->d_pk + 2 * ne;
+  p.off = base + 16 * ne;
+  p.row_map = base + 16 * ne + lanes + 1;
+  p.pw = t->d_pkw;
+  p.nsteps = pl->nsteps;
+  PackedLaunch &L = t->pl;
+  L.tets = t->d_dev;
+  L.order = nullptr;
+  L.ntets = 1;
+  L.reg = packed_degree(t->host.dx);
+  L.v1 = t->host.boundary == ILU_BOUNDARY_V1;
+  return ILU_OK;
+}
+
 ilu_status upload(ilu_tet t) {
   HostTet &h = t->host;
   CK(cudaSetDevice(t->device), "cudaSetDevice");
@@ -344,6 +428,17 @@ ilu_status upload(ilu_tet t) {
   if (t->use_band) {
     ilu_status bs = upload_band(t, t->requested_slabs);
     if (bs != ILU_OK) return bs;
+  }
+  // packed kernels: one CTA per tet (see packed.h); measured faster than the
+  // slab kernels for a single tet up to level 6 (F32 sweeps at L5/L6/L7/L8:
+  // 0.086/0.21/1.08/7.98 ms packed, 0.14/0.30/0.63/1.73 ms slab), and the
+  // batch kernel of choice (a CTA per tet, no waits between CTAs)
+  t->use_packed = !t->use_band && t->precision != ILU_F64 && h.dx <= kPackedMaxDegree &&
+                  h.L <= kPackedMaxLevel &&
+                  (t->kernel_choice == ILU_KERNEL_PACKED || (t->kernel_choice == ILU_KERNEL_AUTO && h.L <= 6));
+  if (t->use_packed) {
+    ilu_status ps = upload_packed(t);
+    if (ps != ILU_OK) return ps;
   }
   CK(cudaMalloc(&t->d_partials, sizeof(double) * t->nblocks), "cudaMalloc partials");
   t->norms_cap = 0;
@@ -412,6 +507,10 @@ ilu_status upload_tables(ilu_tet t) {
   if (nb)
     CK(cudaMemcpy(t->d_tabB, f64 ? (const void *)h.tabB64.data() : (const void *)h.tabB32.data(), nb * es,
                   cudaMemcpyHostToDevice), "upload tables");
+  if (t->use_packed) {  // so do the packed kernels' compact copies
+    ilu_status ps = upload_packed_tables(t);
+    if (ps != ILU_OK) return ps;
+  }
   if (t->tabulate) {  // the tabulated values follow the new polynomials
     CK(launch_tabulate(t->dev, t->d_valsF, t->d_valsB, cudaStreamPerThread), "tabulation launch");
     CK(cudaStreamSynchronize(cudaStreamPerThread), "tabulation");
@@ -536,11 +635,21 @@ ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStre
   int used = 0;
   {
     Traced tr(t, 0, st);
-    CK(launch_residual(t->dev, t->kind(), x, b, t->d_w, t->d_partials, t->nblocks, &used, st), "residual launch");
+    CK(launch_residual(t->dev, t->kind(), x, b, t->d_w, t->d_partials, t->nblocks, &used, st, t->use_packed),
+       "residual launch");
   }
   if (d_norm_out) {
     t->launches++;
     CK(launch_norm_finish(t->d_partials, used, d_norm_out, st), "norm launch");
+  }
+  if (t->use_packed) {  // forward and backward substitution in one launch (traced as the forward)
+    {
+      Traced tr(t, 1, st);
+      CK(launch_packed(t->pl, st), "packed substitution launch");
+    }
+    Traced tr(t, 2, st);  // x += w (traced as the backward)
+    CK(launch_packed_io(0, t->precision != ILU_F32, t->d_dev, nullptr, 1, used, nullptr, x, st), "update launch");
+    return ILU_OK;
   }
   {
     Traced tr(t, 1, st);
@@ -577,6 +686,19 @@ ilu_status precond(ilu_tet t, const void *r, void *z, cudaStream_t st) {
       t->launches++;
       CK(launch_band_update(t->kind(), t->d_dev, t->band_tprefix, 1, t->band_ntiles, nullptr, z, st), "update launch");
     }
+    return ILU_OK;
+  }
+  if (t->use_packed) {  // r into the packed array, the substitutions, z = their result
+    const int nb = residual_blocks(t->host.N);
+    t->launches++;
+    CK(launch_packed_io(1, vf64, t->d_dev, nullptr, 1, nb, nullptr, const_cast<void *>(r), st), "copy launch");
+    CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
+    {
+      Traced tr(t, 1, st);
+      CK(launch_packed(t->pl, st), "packed substitution launch");
+    }
+    Traced tr(t, 2, st);
+    CK(launch_packed_io(0, vf64, t->d_dev, nullptr, 1, nb, nullptr, z, st), "update launch");
     return ILU_OK;
   }
   CK(launch_copy(vf64, wf64, r, t->d_w, n, st), "copy launch");
@@ -646,6 +768,8 @@ bool tet_view(ilu_tet t, TetView *v) {
   v->reg = t->wave_reg();
   v->nnodes = t->nnodes();
   v->failed = t->failed;
+  v->packed = t->use_packed;
+  v->packed_steps = t->use_packed ? 2 * t->dev.pk.nsteps : 0;
   return true;
 }
 WaveGeom wave_geom(int N, int kind, int dxp, int reg, bool fwd, int requested) {
@@ -727,7 +851,11 @@ ilu_status ilu_setup(const double macro_tet[12], int level, const ilu_coeff *coe
   ilu_opts_default(&o);
   if (opts) o = *opts;
   if (o.precision < 0 || o.precision > 2) return fail(ILU_EINVAL, "unknown precision");
-  if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_BAND) return fail(ILU_EINVAL, "unknown kernel choice");
+  if (o.kernel < ILU_KERNEL_AUTO || o.kernel > ILU_KERNEL_PACKED) return fail(ILU_EINVAL, "unknown kernel choice");
+  if (o.kernel == ILU_KERNEL_PACKED && (level > kPackedMaxLevel || o.precision == ILU_F64))
+    return fail(ILU_EINVAL, "the packed kernels take FP32/MIXED sweeps up to level 8");
+  if (o.kernel == ILU_KERNEL_PACKED && (o.deg[0] >= 0 ? o.deg[0] : poly_degree) > kPackedMaxDegree)
+    return fail(ILU_EINVAL, "the packed kernels take row (x) degrees up to 6");
   if (o.factor != ILU_FACTOR_ILU0 && o.factor != ILU_FACTOR_SGS) return fail(ILU_EINVAL, "unknown factor choice");
   if (o.stencil < ILU_STENCIL_AUTO || o.stencil > ILU_STENCIL_STORED) return fail(ILU_EINVAL, "unknown stencil choice");
   if (o.orient != ILU_ORIENT_GIVEN && o.orient != ILU_ORIENT_LFA) return fail(ILU_EINVAL, "unknown orientation choice");
@@ -1044,6 +1172,28 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
     if (st != ILU_OK) { t->failed = true; return st; }
     rel = std::sqrt(std::max(t->h_scal[0], 0.0)) / bn;
   }
+}
+
+ilu_status ilu_packed_schedule(int level, int forward, int lanes, int *nsteps, int *lanes_out, int *entries,
+                               int *lane_off) {
+  if (!nsteps || !lanes_out) return fail(ILU_EINVAL, "null argument");
+  if (level < 2 || level > kPackedMaxLevel) return fail(ILU_EINVAL, "the packed schedules cover levels 2 to 8");
+  if (lanes < 0 || lanes > 511) return fail(ILU_EINVAL, "lanes must be 0 (the kernels' count) or 1..511");
+  std::string err;
+  PackedPlan own;
+  const PackedPlan *p = nullptr;
+  if (lanes == 0 || lanes == kPackedLanes) {
+    p = packed_plan_cached(1 << level, &err);
+  } else if (make_packed_plan(1 << level, lanes, &own, &err)) {
+    p = &own;
+  }
+  if (!p) return fail(ILU_EINVAL, err);
+  *nsteps = p->nsteps;
+  *lanes_out = p->lanes;
+  const std::vector<PackedEntry> &e = forward ? p->fwd : p->bwd;
+  if (entries) std::memcpy(entries, e.data(), sizeof(PackedEntry) * e.size());
+  if (lane_off) std::memcpy(lane_off, p->lane_off.data(), sizeof(int) * p->lane_off.size());
+  return ILU_OK;
 }
 
 ilu_status ilu_profile_enable(ilu_tet t, int enable) {

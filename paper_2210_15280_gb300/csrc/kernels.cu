@@ -16,6 +16,7 @@
 #include <utility>
 
 #include "kernels.cuh"
+#include "packed.h"
 #include "stencil.cuh"
 
 namespace ilu {
@@ -35,16 +36,18 @@ struct StencilData {
   int64_t astride;
 };
 
-// MODE of the operator: 0 constant stencil, 1 assembled on the fly from
-// kappa, 2 stored coefficients (same values as 1)
-constexpr int kOpConst = 0, kOpStar = 1, kOpStored = 2;
+// MODE of the operator (kernels.cuh): constant stencil, assembled on the fly
+// from kappa, or stored coefficients (the same values as on the fly)
 
 // r = b - A x at the interior points x0 + lane of row (y, z) (one warp, one
 // 32-point chunk of the row); returns this lane's share of ||r||^2
+// (pmap non-null: r goes to the packed array pw instead, at the slot of the
+// point's row, pmap[row id] = forward first step | lane << 20)
 template <typename TX, typename TR, typename TW, int MODE>
 __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, int y, int z, int x0, int lane,
                                                  const TX *__restrict__ x, const TX *__restrict__ b,
-                                                 TW *__restrict__ r) {
+                                                 TW *__restrict__ r, const int *__restrict__ pmap = nullptr,
+                                                 float *__restrict__ pw = nullptr) {
   double acc2 = 0.0;
   if (y + z > N - 2) return acc2;
   const int n = N - 1 - y - z;
@@ -103,29 +106,37 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, int N, in
       kq[14] = kap[rt + xx - 1];
       star_apply_all(std::make_integer_sequence<int, 15>{}, res, kq, xv, t.Wstar);
     }
-    r[r0 + xx] = (TW)res;
+    if (pmap) {
+      const int m = pmap[row_id(N, y, z)];
+      pw[packed_index((m & 0xfffff) + xx - 1, m >> 20)] = (float)res;
+    } else {
+      r[r0 + xx] = (TW)res;
+    }
     acc2 += (double)res * (double)res;
   }
   return acc2;
 }
 
-// One tet: one warp per 32-point chunk of an interior row (the chunk list
-// balances rows of every length), 8 chunks per block, per-block partial norms.
+// One tet: a warp per kResidualCPW consecutive 32-point chunks of interior
+// rows (the chunk list balances rows of every length), 8 warps per block,
+// per-block partial norms.
 template <typename TX, typename TR, typename TW, int MODE>
-__global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__restrict__ x,
+__global__ void __launch_bounds__(256, MODE == kOpStar ? 1 : 4) residual_kernel(DevTet t, const TX *__restrict__ x,
                                                        const TX *__restrict__ b, TW *__restrict__ r,
-                                                       double *__restrict__ partials) {
+                                                       double *__restrict__ partials, bool packed) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the constant stencil, converted once per block to the residual type
   __shared__ TR sA15[15];
   if (threadIdx.x < 15) sA15[threadIdx.x] = (TR)t.A15[threadIdx.x];
   __syncthreads();
   const StencilData sd{sA15, t.Wstar, t.kappa, t.astore, t.astride};
-  const int ci = blockIdx.x * 8 + warp;
   double acc2 = 0.0;
-  if (ci < t.nchunks) {
-    const int ch = t.chunks[ci];
-    acc2 = residual_chunk<TX, TR, TW, MODE>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b, r);
+  const int c0 = (blockIdx.x * 8 + warp) * kResidualCPW;  // this warp's consecutive chunks
+#pragma unroll 1
+  for (int k = 0; k < kResidualCPW && c0 + k < t.nchunks; ++k) {
+    const int ch = t.chunks[c0 + k];
+    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b,
+                                             r, packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
   }
   // deterministic block reduction of the squared norm
 #pragma unroll
@@ -140,13 +151,16 @@ __global__ void __launch_bounds__(256) residual_kernel(DevTet t, const TX *__res
   }
 }
 
-// Many tets: 1-D grid, tet i owns blocks [bprefix[i], bprefix[i+1]) laid out
-// as its single-tet grid; the result goes to the tet's scratch w.
-template <typename TX, typename TR, typename TW>
-__global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__restrict__ tets,
-                                                             const int *__restrict__ bprefix, int n,
-                                                             const TX *const *__restrict__ xs,
-                                                             const TX *const *__restrict__ bs) {
+// Many tets whose operators come the same way (MODE): 1-D grid, tet
+// order[i] owns blocks [bprefix[i], bprefix[i+1]) laid out as its single-tet
+// grid; the result goes to the tet's packed array if it has one, else to its
+// scratch w.  One launch per operator kind keeps the register count of each
+// kernel that of its own arithmetic.
+template <typename TX, typename TR, typename TW, int MODE>
+__global__ void __launch_bounds__(256, MODE == kOpStar ? 1 : 4)
+    residual_batch_kernel(const DevTet *__restrict__ tets, const int *__restrict__ order,
+                          const int *__restrict__ bprefix, int n, const TX *const *__restrict__ xs,
+                          const TX *const *__restrict__ bs) {
   int lo = 0, hi = n - 1;
   const int blk = blockIdx.x;
   while (lo < hi) {
@@ -154,28 +168,29 @@ __global__ void __launch_bounds__(256) residual_batch_kernel(const DevTet *__res
     if (bprefix[mid] <= blk) lo = mid;
     else hi = mid - 1;
   }
-  const DevTet &tg = tets[lo];
+  const int ti = order[lo];
+  const DevTet &tg = tets[ti];
   // the block's stencil weights in shared memory (reading them from the
   // device array would keep all 100 live in registers)
   __shared__ double sW[kStarPairs];
   __shared__ TR sA[15];
-  for (int i = threadIdx.x; i < kStarPairs; i += blockDim.x) sW[i] = tg.Wstar[i];
+  if (MODE == kOpStar)
+    for (int i = threadIdx.x; i < kStarPairs; i += blockDim.x) sW[i] = tg.Wstar[i];
   if (threadIdx.x < 15) sA[threadIdx.x] = (TR)tg.A15[threadIdx.x];
   __syncthreads();
   const int N = tg.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ci = (blk - bprefix[lo]) * 8 + warp;
-  if (ci >= tg.nchunks) return;  // no block-wide synchronisation follows
-  const int ch = tg.chunks[ci];
+  const int c0 = ((blk - bprefix[lo]) * 8 + warp) * kResidualCPW;
   TW *r = reinterpret_cast<TW *>(tg.w);
   const StencilData sd{sA, sW, tg.kappa, tg.astore, tg.astride};
-  const int y = (ch >> 10) & 1023, z = ch >> 20, x0 = 1 + 32 * (ch & 1023);
-  if (tg.const_kappa)
-    residual_chunk<TX, TR, TW, kOpConst>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
-  else if (tg.astore)
-    residual_chunk<TX, TR, TW, kOpStored>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
-  else
-    residual_chunk<TX, TR, TW, kOpStar>(sd, N, y, z, x0, lane, xs[lo], bs[lo], r);
+  const int *pmap = tg.pk.pw ? tg.pk.row_map : nullptr;
+  const TX *xv = xs[ti], *bv = bs[ti];
+#pragma unroll 1
+  for (int k = 0; k < kResidualCPW && c0 + k < tg.nchunks; ++k) {  // no block-wide synchronisation follows
+    const int ch = tg.chunks[c0 + k];
+    residual_chunk<TX, TR, TW, MODE>(sd, N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, xv, bv, r, pmap,
+                                     tg.pk.pw);
+  }
 }
 
 // ------------------------------------------------- solver vector helpers --
@@ -281,7 +296,7 @@ int residual_chunks(int N) {
     for (int y = 1; y <= N - 2 - z; ++y) n += (N - 1 - y - z + 31) / 32;
   return n;
 }
-int residual_blocks(int N) { return (residual_chunks(N) + 7) / 8; }
+int residual_blocks(int N) { return (residual_chunks(N) + 8 * kResidualCPW - 1) / (8 * kResidualCPW); }
 int rowgrid_blocks(int N) { return ((N - 3 + 7) / 8) * (N - 3); }
 void residual_chunk_list(int N, int *out) {
   int i = 0;
@@ -291,8 +306,9 @@ void residual_chunk_list(int N, int *out) {
 }
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
-                            int nblocks_cap, int *nblocks_used, cudaStream_t st) {
-  const int nb = (t.nchunks + 7) / 8;
+                            int nblocks_cap, int *nblocks_used, cudaStream_t st, bool packed) {
+  if (packed && (!t.pk.pw || kind == kSweepF64)) return cudaErrorInvalidValue;
+  const int nb = (t.nchunks + 8 * kResidualCPW - 1) / (8 * kResidualCPW);
   if (nb > nblocks_cap || !t.chunks) return cudaErrorInvalidValue;
   if (nblocks_used) *nblocks_used = nb;
   if (nb == 0) return cudaSuccess;
@@ -303,7 +319,7 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
     using TR = decltype(tr);
     using TW = decltype(tw);
     residual_kernel<TX, TR, TW, decltype(m)::value><<<grid, 256, 0, st>>>(t, (const TX *)x, (const TX *)b,
-                                                                          (TW *)r_out, partials);
+                                                                          (TW *)r_out, partials, packed);
   };
   auto by_mode = [&](auto tx, auto tr, auto tw) {
     if (mode == kOpConst) go(tx, tr, tw, std::integral_constant<int, kOpConst>{});
@@ -316,18 +332,24 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n, int total_blocks, int kind,
-                                  const void *const *xs, const void *const *bs, cudaStream_t st) {
+cudaError_t launch_residual_batch(const DevTet *tets, const int *order, const int *bprefix, int n, int total_blocks,
+                                  int kind, int op, const void *const *xs, const void *const *bs, cudaStream_t st) {
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
-  if (kind == kSweepF64)
-    residual_batch_kernel<double, double, double><<<total_blocks, 256, 0, st>>>(
-        tets, bprefix, n, reinterpret_cast<const double *const *>(xs), reinterpret_cast<const double *const *>(bs));
-  else if (kind == kSweepMixed)
-    residual_batch_kernel<double, double, float><<<total_blocks, 256, 0, st>>>(
-        tets, bprefix, n, reinterpret_cast<const double *const *>(xs), reinterpret_cast<const double *const *>(bs));
-  else
-    residual_batch_kernel<float, float, float><<<total_blocks, 256, 0, st>>>(
-        tets, bprefix, n, reinterpret_cast<const float *const *>(xs), reinterpret_cast<const float *const *>(bs));
+  auto go = [&](auto tx, auto tr, auto tw, auto m) {
+    using TX = decltype(tx);
+    using TR = decltype(tr);
+    using TW = decltype(tw);
+    residual_batch_kernel<TX, TR, TW, decltype(m)::value><<<total_blocks, 256, 0, st>>>(
+        tets, order, bprefix, n, reinterpret_cast<const TX *const *>(xs), reinterpret_cast<const TX *const *>(bs));
+  };
+  auto by_op = [&](auto tx, auto tr, auto tw) {
+    if (op == kOpConst) go(tx, tr, tw, std::integral_constant<int, kOpConst>{});
+    else if (op == kOpStored) go(tx, tr, tw, std::integral_constant<int, kOpStored>{});
+    else go(tx, tr, tw, std::integral_constant<int, kOpStar>{});
+  };
+  if (kind == kSweepF64) by_op(double{}, double{}, double{});
+  else if (kind == kSweepMixed) by_op(double{}, double{}, float{});
+  else by_op(float{}, float{}, float{});
   return cudaGetLastError();
 }
 

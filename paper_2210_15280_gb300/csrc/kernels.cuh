@@ -36,6 +36,18 @@ struct BandDev {
   int ncta, ntiles, Z;
 };
 
+// Row schedules of the packed substitutions (packed.h): the PackedEntry
+// records (two int4 each) of either pass grouped by lane, the lane offsets
+// (the same for both), per row id its forward first step | lane << 20, the
+// packed step-major array [nsteps][kPackedLanes] and its step count.
+struct PackedDev {
+  const int4 *ent_f, *ent_b;
+  const int *off;
+  const int *row_map;
+  float *pw;
+  int nsteps;
+};
+
 // Everything a kernel needs to know about one tet.  Plain old data so that it
 // can live in a device array for batched launches.
 struct DevTet {
@@ -53,6 +65,9 @@ struct DevTet {
   double A15[15];    // constant stencil
   double Wstar[100]; // edge-star weights (variable coefficient)
   BandDev band;      // FP32 band sweeps (null info when not used)
+  PackedDev pk;      // packed substitution schedules (null when not used)
+  const void *pkF;   // packed kernels' FP32 row polynomials: [row][k = 0..dx][4 function pairs] float2,
+  const void *pkB;   // forward and backward (null when not used)
   const int *chunks; // residual work list: z << 20 | y << 10 | chunk (32 points of a row)
   int nchunks;
   const void *astore;    // variable kappa, stored operator: coefficient of direction d (d != centre) of
@@ -78,13 +93,20 @@ struct LaunchStatus {
 // X = element type of x and b, R = type the residual is computed in
 enum SweepKind { kSweepF64 = 0, kSweepF32 = 1, kSweepMixed = 2 };
 
+// packed: write r into the tet's packed array (t.pk) instead of r_out
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
-                            int nblocks_cap, int *nblocks_used, cudaStream_t st);
-// Residual of many tets in one launch: tet i owns blocks [bprefix[i], bprefix[i+1])
-// of the 1-D grid (bprefix[n] = total, residual_blocks(N_i) each); tets and
-// the pointer arrays are device memory.  Writes w of each tet; no norms.
-cudaError_t launch_residual_batch(const DevTet *tets, const int *bprefix, int n, int total_blocks, int kind,
-                                  const void *const *xs, const void *const *bs, cudaStream_t st);
+                            int nblocks_cap, int *nblocks_used, cudaStream_t st, bool packed = false);
+// How a tet's residual gets its operator: the constant stencil, assembled on
+// the fly from kappa at the grid points, or the stored coefficients.
+constexpr int kOpConst = 0, kOpStar = 1, kOpStored = 2;
+inline int residual_op(const DevTet &t) { return t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar); }
+// Residual of many tets with the same residual_op in one launch: tet
+// order[i] owns blocks [bprefix[i], bprefix[i+1]) of the 1-D grid (bprefix[n]
+// = total, residual_blocks(N) each); tets, order, bprefix and the per-tet
+// pointer arrays (indexed by tet) are device memory.  Writes w of each tet,
+// or its packed array if it has one; no norms.
+cudaError_t launch_residual_batch(const DevTet *tets, const int *order, const int *bprefix, int n, int total_blocks,
+                                  int kind, int op, const void *const *xs, const void *const *bs, cudaStream_t st);
 cudaError_t launch_norm_finish(const double *partials, int n, double *out, cudaStream_t st);
 // assemble the 14 off-diagonal coefficients of every interior row (variable
 // kappa) into A (14 planes of t.astride doubles), the values the on-the-fly
@@ -145,7 +167,8 @@ constexpr int kTabulatedMaxLevel = 9;
 // Fill valsF / valsB (8 doubles per grid point each) from the FP64 row
 // tables of t, with the arithmetic of the substitutions' own evaluation.
 cudaError_t launch_tabulate(const DevTet &t, double *valsF, double *valsB, cudaStream_t st);
-int residual_blocks(int N);  // blocks of the residual launch (8 row chunks each)
+constexpr int kResidualCPW = 4;  // consecutive 32-point row chunks per warp of the residual launches
+int residual_blocks(int N);  // blocks of the residual launch (8 warps of kResidualCPW row chunks each)
 int rowgrid_blocks(int N);   // blocks of the row-per-warp reductions (interior norm)
 int residual_chunks(int N);
 void residual_chunk_list(int N, int *out);
@@ -176,6 +199,29 @@ cudaError_t launch_band_in(int kind, int mode, const DevTet *tets, const int *tp
 cudaError_t launch_band_update(int kind, const DevTet *tets, const int *tprefix, int ntets, int total_tiles,
                                void *const *xs, void *x1, cudaStream_t st);
 
+// ---- packed substitutions (packed.cu): one CTA per tet runs its forward and
+// backward substitution on the tet's packed array (which holds r on entry and
+// the backward result on exit).  reg: the degree of the packed row tables (3
+// or 6); v1: some tet uses boundary variant V1.  order (device, nullable): the
+// tet of each CTA.
+struct PackedLaunch {
+  const DevTet *tets;
+  const int *order;
+  int ntets;
+  int reg;
+  bool v1;
+};
+size_t packed_smem_bytes(int reg);
+cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st);
+// Between a tet's lexicographic vectors and its packed array, over the
+// residual chunk list (tet i owns blocks [bprefix[i], bprefix[i+1]) of the
+// grid, or every block for a single tet when bprefix is null): mode 0 adds
+// the packed values to x (per tet in xs, or x1), mode 1 copies the interior
+// of x (a vector, converted to float) into the packed array.  f64: x is
+// double, else float.
+cudaError_t launch_packed_io(int mode, bool f64, const DevTet *tets, const int *bprefix, int ntets, int total_blocks,
+                             void *const *xs, void *x1, cudaStream_t st);
+
 // ---- host-side views shared by the entry-point files (capi.cu defines them)
 
 // what a batch needs to know of a tet handle
@@ -185,6 +231,8 @@ struct TetView {
   int reg;  // WaveLaunch.reg code of its substitutions
   size_t nnodes;
   bool failed;
+  bool packed;  // its substitutions run on the packed kernels (cost: steps of both passes)
+  int packed_steps;
 };
 bool tet_view(ilu_tet_s *t, TetView *v);
 // partition of one substitution (requested > 0: about that many slabs)

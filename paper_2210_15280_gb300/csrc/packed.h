@@ -1,0 +1,84 @@
+// packed.h -- the packed substitution kernels of the FP32 sweeps (packed.cu)
+// and their host-side row schedules (packed_plan.cpp).
+//
+// A packed launch gives every macro-tetrahedron one CTA of kPackedLanes
+// threads, which runs the tet's whole forward substitution and then its whole
+// backward substitution (Alg. 2 of arXiv 2210.15280) without waiting on any
+// other CTA.  Inside the CTA the interior rows (y, z) are packed onto the
+// lanes: a lane owns one row at a time, keeps that row's surrogate
+// polynomials in registers and computes one point of it per step; the CTA
+// advances one step per block barrier.
+//
+// The schedule -- which lane owns which row from which step on -- is computed
+// on the host once per level: rows in the order of their natural first
+// hyperplane x + 2y + 3z go to the lane that frees up first, with one delay
+// for all later rows whenever no lane is free, so that every producer row
+// keeps a delay no larger than that of its consumers and dependencies keep
+// their order.  The backward substitution runs the same schedule backwards in
+// time (step T - 1 - tau of the forward pass): every forward dependency,
+// reversed, is a backward one, so the reversed schedule is valid, and every
+// row stays on its lane.
+//
+// Packed layout.  Point (x, y, z) of a row that starts at forward step s on
+// lane l has the slot (s + x - 1, l) of a float array of T steps x
+// kPackedLanes lanes in four-step blocks: step s of lane l at
+// ((s / 4) * kPackedLanes + l) * 4 + s % 4 (packed_index).  The residual
+// writes r there, the forward pass replaces it by its result and the
+// backward pass by its own; an update kernel adds the latter to x.  The
+// passes move one 16-byte block per lane every four steps, the lanes of a warp
+// on consecutive blocks; a row's consecutive points fill whole blocks.
+#pragma once
+#include <string>
+#include <vector>
+
+namespace ilu {
+
+constexpr int kPackedLanes = 384;  // threads (row lanes) of a packed CTA
+constexpr int kPackedRing = 32;    // steps of each lane's results kept in shared memory
+constexpr int kPackedQueue = 8;    // input queue slots per lane
+constexpr int kPackedPre = 7;      // input prefetch distance in steps (below the slot count: the
+                                   // entry read at a step is never the one being refilled)
+constexpr int kPackedMaxLevel = 8; // highest level the packed kernels take
+constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fill the shared memory)
+
+// A producer code tells a consumer row where the values of one of its three
+// producer rows are (bits 30-31 the mode): the producer's lane in bits 0-8,
+// the step distance k0 of the first value the consumer reads at a step (the
+// second is written one step later) in bits 9-29, and
+//   kProdNone    no such interior row (the values are masked to 0);
+//   kProdRing    k0 <= kPackedRing - 1: read from the producer lane's ring;
+//   kProdGlobal  further behind: read back from the packed array in global
+//                memory, prefetched like the inputs.
+enum { kProdNone = 0, kProdRing = 1, kProdGlobal = 2 };
+inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 9); }
+
+// One row of a schedule (32 bytes): step of its first point; n | y << 10 |
+// z << 20 (n = points of the row); grid index of its point x = 0; row id;
+// the three producer codes; 1 if a producer is kProdGlobal, else 0.
+struct PackedEntry {
+  int start, nyz, gb, rid, p[3], far;
+};
+
+// slot of step s, lane l in the packed array
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline size_t packed_index(int s, int l) { return ((size_t)(s >> 2) * kPackedLanes + l) * 4 + (s & 3); }
+
+struct PackedPlan {
+  int N = 0, lanes = 0, nsteps = 0;  // nsteps = T, the steps of either pass
+  std::vector<PackedEntry> fwd, bwd;  // grouped by lane, each lane's rows in step order
+  std::vector<int> lane_off;          // lanes + 1 offsets into either list
+  std::vector<int> row_map;           // per row id: forward first step | lane << 20
+};
+
+// Schedule of a level-L tet (N = 2^L) on `lanes` lanes.  The forward
+// producers of row (y, z) are (y-1, z), (y, z-1), (y+1, z-1); the backward
+// ones (y+1, z), (y, z+1), (y-1, z+1).  False (with err) if a check of the
+// schedule fails.
+bool make_packed_plan(int N, int lanes, PackedPlan *out, std::string *err);
+// The plan on kPackedLanes lanes, computed once per level and kept for the
+// life of the process; null (with err) if the schedule fails.
+const PackedPlan *packed_plan_cached(int N, std::string *err);
+
+}  // namespace ilu

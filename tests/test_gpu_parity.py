@@ -73,13 +73,14 @@ def test_f64_sweeps_match_oracle(g, orc, level, kind, deg):
     assert np.allclose(ng, no, rtol=1e-12)
 
 
-@pytest.mark.parametrize("kernel", ["SLAB", "BAND"])
+@pytest.mark.parametrize("kernel", ["SLAB", "BAND", "PACKED"])
 @pytest.mark.parametrize("prec", ["F32", "MIXED"])
 @pytest.mark.parametrize("level,kind,deg", [(3, "const", 2), (4, "const", 4), (5, "sinprod", 6), (6, "const", 6),
                                             (6, "kappa_i", 3), (7, "sinprod", 6)])
 def test_reduced_precision_per_sweep(g, orc, prec, level, kind, deg, kernel):
     """Each sweep, started from the oracle's current iterate, lands within
-    1e-5 (relative) of the oracle's next iterate (both substitution kernels)."""
+    1e-5 (relative) of the oracle's next iterate (every substitution kernel
+    family)."""
     P, co, pr = problem(orc, level, 51 + level, kind, deg)
     N = 2 ** level
     p = getattr(g, prec)
@@ -247,7 +248,8 @@ def test_library_fit_end_to_end(g, orc):
     assert rel(xd.cpu().numpy(), xo) < 1e-5
 
 
-@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND"), ("F32", "BAND")])
+@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND"), ("F32", "BAND"),
+                                         ("MIXED", "PACKED"), ("F32", "PACKED")])
 def test_sgs_smoother_matches_oracle(g, orc, prec, kernel):
     """The symmetric Gauss-Seidel comparison smoother (ilu_opts.factor = SGS)
     runs through the same surrogate pipeline and kernels."""
@@ -337,7 +339,8 @@ def test_tabulated_values_bitwise_equal_on_the_fly(g, level, kind, deg, boundary
     (3, "const", "F64", "SLAB"), (4, "sinprod", "F64", "SLAB"), (5, "kappa_i", "F64", "SLAB"),
     (6, "sinprod", "F64", "SLAB"), (5, "sinprod", "MIXED", "SLAB"), (7, "const", "MIXED", "SLAB"),
     (6, "kappa_i", "F32", "SLAB"), (5, "sinprod", "MIXED", "BAND"), (7, "const", "MIXED", "BAND"),
-    (6, "kappa_i", "F32", "BAND")])
+    (6, "kappa_i", "F32", "BAND"), (5, "sinprod", "MIXED", "PACKED"), (7, "const", "MIXED", "PACKED"),
+    (6, "kappa_i", "F32", "PACKED")])
 def test_v1_boundary_variant_matches_oracle(g, orc, level, kind, prec, kernel):
     """Variant V1: the stored exact factors (L^p_d and 1/D^p) at the
     cell-boundary points, surrogates elsewhere (the oracle's v1_factors)."""

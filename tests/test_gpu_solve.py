@@ -31,7 +31,7 @@ def exact_solution(orc, pr, N, b, xbd):
     return x
 
 
-@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND")])
+@pytest.mark.parametrize("prec,kernel", [("F64", "AUTO"), ("MIXED", "SLAB"), ("MIXED", "BAND"), ("MIXED", "PACKED")])
 @pytest.mark.parametrize("method", ["RICHARDSON", "PCG"])
 def test_solve_reaches_tolerance(g, orc, prec, method, kernel):
     level, deg, N = 4, 4, 16

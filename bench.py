@@ -264,10 +264,12 @@ def sharded_oracle_sweeps(rank, world, dist, n=10):
     return sorted((p for part in parts for p in part), key=lambda p: p[0])
 
 
-def batch_workload(args, g, torch, rank=0, world=1, dist=None):
-    """256 tets, one autotuned batch, one graph replay per step.  On several
-    GPUs each rank sweeps its share of the tets (shard_of) and the line
-    reports all ranks' points over the slowest rank's time."""
+def batch_workload(args, g, torch, rank=0, world=1, dist=None, compact=False):
+    """256 tets, one batch, one graph replay per step.  On several GPUs each
+    rank sweeps its share of the tets (shard_of) and the line reports all
+    ranks' points over the slowest rank's time.  Beside it (one GPU): the same
+    tets swept one handle after another, in FP32 and in plain FP64.
+    `compact`: at most 20 steps, the sub-object of the default line."""
     from concurrent.futures import ThreadPoolExecutor
     n = 256
     mesh = si.macro_mesh(6, n_tets=n)
@@ -286,6 +288,8 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None):
     bs = [torch.tensor(v, device="cuda") for v in bh]
     B = g.Batch(tets)
     W, K = max(3, args.warmup), max(1, args.steps)
+    if compact:
+        K = min(K, 20)
     for _ in range(W):
         B.smooth(xs, bs, 1)
     torch.cuda.synchronize()
@@ -323,6 +327,23 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None):
     nbytes = sum(v.numel() for v in xs) * 4
     achieved = idof * 24 / (total_ms / K / 1e3) / 1e9  # F32 sweep: 24 algorithmic bytes per DoF (this rank)
     hbm, src = peaks()
+    per_tet = None
+    if world == 1:
+        per_tet = one_by_one(g, torch, tets, xs, bs, mesh, levels, degs, W, min(K, 5))
+        per_tet["batch_speedup_vs_f32_one_by_one"] = per_tet["f32_ms_per_sweep"] / (total_ms / K)
+        per_tet["batch_speedup_vs_f64_one_by_one"] = per_tet["f64_ms_per_sweep"] / (total_ms / K)
+    B.close()
+    for t in tets:
+        t.close()
+    if compact:
+        return {"value": value, "unit": UNIT, "ms_per_step": total_ms / K, "steps": K, "dtype": "f32",
+                "workload": f"batch of {n} macro-tets, levels 5-8, degrees 4-6, {idof_all} interior DoF, "
+                            "packed kernels, one graph replay per sweep",
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "kernel": "whole sweep at 24 B/DoF", "peak_source": src},
+                "depth": {"note": "the level-8 tets' packed substitutions bound the batch (one SM each)"},
+                "one_by_one": per_tet,
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes}}
     return {"metric": "smoother DoF-sweeps/s (batch of 256 macro-tets, FP32 sweeps)", "value": value, "unit": UNIT,
             "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -334,20 +355,78 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "whole sweep (residual + forward + backward)", "peak_source": src},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
-                       "samples": clk["samples"]}}
+                       "samples": clk["samples"]},
+            "one_by_one": per_tet}
 
 
-def level9_workload(args, g, torch):
-    """Single L9 tet, F32 and F64 sweeps, whole-sweep roofline."""
+def one_by_one(g, torch, tets, xs, bs, mesh, levels, degs, W, K):
+    """The batch's tets swept one handle after another (one ilu_smooth call
+    per tet, same stream): with the batch's FP32 handles, and with plain FP64
+    handles (default kernels, matrix-free)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(ts, xv, bv):
+        for _ in range(W):
+            for t, x, b in zip(ts, xv, bv):
+                t.smooth(x, b, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            for t, x, b in zip(ts, xv, bv):
+                t.smooth(x, b, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    f32 = run(tets, xs, bs)
+    with ThreadPoolExecutor(8) as ex:
+        t64 = list(ex.map(lambda k: g.Tet(mesh[k], int(levels[k]), coeff=g.make_coeff("const"),
+                                          poly_degree=int(degs[k]), precision=g.F64,
+                                          stencil=g.STENCIL_ON_THE_FLY, values=g.VALUES_ON_THE_FLY,
+                                          device=torch.cuda.current_device()), range(len(tets))))
+    x64 = [torch.zeros(x.numel(), dtype=torch.float64, device="cuda") for x in xs]
+    b64 = [b.double() for b in bs]
+    f64 = run(t64, x64, b64)
+    for t in t64:
+        t.close()
+    return {"f32_ms_per_sweep": f32, "f64_ms_per_sweep": f64, "sweeps": K,
+            "how": "one ilu_smooth per tet, all tets in turn on one stream"}
+
+
+def level9_workload(args, g, torch, compact=False):
+    """Single level-9 tet (22.1M interior DoF), kappa = 1, degree 6: F32 and
+    F64 sweeps, both matrix-free (constant stencil, surrogates evaluated in
+    the sweep), against the HBM roofline at 24 (F32) and 56 (F64) algorithmic
+    bytes per DoF; the F32 and MIXED results against the F64 result after
+    two sweeps from the same start with the same polynomials.  `compact`:
+    without the level scan, the sub-object of the default line."""
     level = 9
     nint = interior(level)
     P = si.macro_tet(5)
     out = {}
     hbm, src = peaks()
     W, K = max(3, args.warmup), max(1, min(args.steps, 20))
-    for prec, dt, bpd in [(g.F32, torch.float32, 24), (g.F64, torch.float64, 56)]:
-        t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=6, precision=prec)
-        b = torch.tensor(si.rhs(level, 6), dtype=dt, device="cuda")
+    mf = dict(stencil=g.STENCIL_ON_THE_FLY, values=g.VALUES_ON_THE_FLY)
+    coefs = None
+    x0 = si.boundary_data(level, 7)
+    b_h = si.rhs(level, 6)
+    two = {}
+    for name, prec, dt, bpd in [("F64", g.F64, torch.float64, 56), ("F32", g.F32, torch.float32, 24),
+                                ("MIXED", g.MIXED, torch.float64, 24)]:
+        t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=6, precision=prec, **mf)
+        if coefs is None:
+            coefs = t.export_surrogate()
+        else:
+            t.import_surrogate(coefs)
+        xe = torch.tensor(x0, dtype=dt, device="cuda")
+        b = torch.tensor(b_h, dtype=dt, device="cuda")
+        t.smooth(xe, b, 2)
+        two[name] = xe.double().cpu().numpy()
+        del xe
+        if name == "MIXED":
+            t.close()
+            break
         x = torch.zeros_like(b)
         t.smooth(x, b, W)
         torch.cuda.synchronize()
@@ -361,15 +440,33 @@ def level9_workload(args, g, torch):
         ms = e0.elapsed_time(e1) / K
         kms, launches = t.profile_read()
         achieved = nint * bpd / (ms / 1e3) / 1e9
-        out[prec] = {"value": nint / (ms / 1e3), "ms_per_step": ms, "achieved_gbs": achieved,
-                     "frac": achieved / hbm, "kernel_ms": [round(v / K, 4) for v in kms],
+        out[name] = {"value": nint / (ms / 1e3), "ms_per_step": ms, "achieved_gbs": achieved,
+                     "frac": achieved / hbm, "kernel_ms_per_launch": [round(v / K, 4) for v in kms],
                      "launches_per_step": launches / K}
         t.close()
-    f = out[g.F32]
+    ref = two["F64"]
+    scale = np.abs(ref).max()
+    err = {f"{nm}_vs_F64_after_2_sweeps": float(np.abs(two[nm] - ref).max() / scale) for nm in ("F32", "MIXED")}
+    f, d = out["F32"], out["F64"]
+    sm_mhz = 2070.0
+    levels = 3 * 2 ** level - 11
+    cyc = g.step_floor(32, 4096)
+    depth = {"steps_per_substitution": levels, "floor_cycles_per_step_one_warp": round(cyc, 1),
+             "us_per_sweep_at_max_clock": round(2 * levels * cyc / (sm_mhz * 1e6) * 1e6, 1)}
+    if compact:
+        return {"value": f["value"], "unit": UNIT, "ms_per_step": f["ms_per_step"], "steps": K, "dtype": "f32",
+                "workload": f"single macro-tet L9 ({nint} interior DoF), kappa=1, deg 6, band kernels, matrix-free",
+                "roofline": {"bound": "hbm", "achieved": f["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                             "frac": f["frac"], "kernel": "whole sweep at 24 B/DoF", "peak_source": src,
+                             "kernel_ms_per_launch": f["kernel_ms_per_launch"]},
+                "depth": depth,
+                "F64": {"value": d["value"], "ms_per_step": d["ms_per_step"], "achieved_gbs": d["achieved_gbs"],
+                        "frac": d["frac"], "bytes_per_dof": 56, "kernel_ms_per_launch": d["kernel_ms_per_launch"]},
+                "error": err}
     # bandwidth scaling: the same F32 sweep at levels 6-8 (slab kernels) and 9 (band kernels)
     scaling = {}
     for lv in [6, 7, 8]:
-        t = g.Tet(P, lv, coeff=g.make_coeff("const"), poly_degree=6, precision=g.F32)
+        t = g.Tet(P, lv, coeff=g.make_coeff("const"), poly_degree=6, precision=g.F32, **mf)
         b = torch.tensor(si.rhs(lv, 6), dtype=torch.float32, device="cuda")
         x = torch.zeros_like(b)
         t.smooth(x, b, W)
@@ -394,16 +491,15 @@ def level9_workload(args, g, torch):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"single macro-tet L9 ({nint} interior DoF), kappa=1, deg 6",
                        "kernels": "band (automatic choice at level 9)", "l2": "inputs larger than L2",
+                       "operator": "constant stencil", "surrogates": "evaluated on the fly",
                        "parallelism": "replicas x1"},
             "roofline": {"bound": "hbm", "achieved": f["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                          "frac": f["frac"], "traffic": None, "kernel": "whole sweep at 24 B/DoF",
-                         "peak_source": src, "kernel_ms_per_launch": f["kernel_ms"]},
-            "f64": {"value": out[g.F64]["value"], "ms_per_step": out[g.F64]["ms_per_step"],
-                    "achieved_gbs": out[g.F64]["achieved_gbs"], "frac": out[g.F64]["frac"],
-                    "kernel_ms_per_launch": out[g.F64]["kernel_ms"],
-                    "surrogate_values": "tabulated at set-up (ilu_opts.values AUTO): the substitutions also "
-                                        "read 2 x 64 B per point, 184 B/DoF in all",
-                    "frac_with_tables": out[g.F64]["frac"] * 184 / 56},
+                         "peak_source": src, "kernel_ms_per_launch": f["kernel_ms_per_launch"]},
+            "depth": depth,
+            "f64": {"value": d["value"], "ms_per_step": d["ms_per_step"], "achieved_gbs": d["achieved_gbs"],
+                    "frac": d["frac"], "kernel_ms_per_launch": d["kernel_ms_per_launch"]},
+            "error": err,
             "f32_level_scaling": scaling,
             "gpu_launches": int(round(f["launches_per_step"] * K))}
 
@@ -641,6 +737,195 @@ def boundary_workload(args, g, torch):
             "height_0.1_z_only": flat_z}
 
 
+
+def time_steps(t, x, b, K, flush, stream, torch):
+    """K sweeps, each bracketed by CUDA events on `stream`, the L2 flushed
+    (256 MiB write) before each; returns the per-step milliseconds."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        t.smooth(x, b, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(e) for a, e in ev]
+
+
+def sweep_variant(g, torch, P, flush, stream, W, K, level=None, prec=None, coeff=COEFF, **opts):
+    """ms per sweep and DoF-sweeps/s of one set-up variant of the default tet,
+    with its per-kernel split (CUDA events around each launch)."""
+    level = LEVEL if level is None else level
+    prec = g.MIXED if prec is None else prec
+    dt = torch.float32 if prec == g.F32 else torch.float64
+    t = g.Tet(P, level, coeff=g.make_coeff(*coeff), poly_degree=DEG, precision=prec,
+              device=torch.cuda.current_device(), **opts)
+    b = torch.tensor(si.rhs(level, RHS_SEED), dtype=dt, device="cuda")
+    x = torch.zeros_like(b)
+    t.smooth(x, b, W)
+    torch.cuda.synchronize()
+    t.profile(True)
+    t.profile_read()
+    ms = statistics.median(time_steps(t, x, b, K, flush, stream, torch))
+    kms, launches = t.profile_read()
+    t.close()
+    return {"ms_per_step": round(ms, 5), "value": interior(level) / (ms / 1e3),
+            "kernel_ms_per_launch": {nm: round(v / K, 5) for nm, v in zip(["residual", "forward", "backward"], kms)}}
+
+
+def depth_bound(g, levels, threads, sm_mhz):
+    """The dependency-depth bound of the substitutions: `levels` barrier
+    steps per substitution (two substitutions per sweep) at the measured
+    cycles of the shortest step body (ilu_step_floor, CTAs of `threads`)."""
+    cyc = g.step_floor(threads, 4096)
+    return {"steps_per_substitution": levels, "floor_cycles_per_step": round(cyc, 1), "floor_threads": threads,
+            "us_per_sweep": round(2 * levels * cyc / (sm_mhz * 1e6) * 1e6, 2)}
+
+
+def error_report(g, torch, P):
+    """Errors of the measured configuration against FP64 references.  Two
+    sweeps of the default tet from the same start in MIXED and in F64
+    (matrix-free, as timed) against the oracle's two sweeps with the same
+    polynomials (the oracle's own fit, imported); then PCG to a relative
+    residual of 1e-8 in MIXED and in F64: iterations, final residuals and the
+    difference of the two solutions."""
+    from oracle import oracle as O
+    N = 2 ** LEVEL
+    pr = O.Problem(P, LEVEL, O.Coeff(*COEFF), deg=DEG)
+    x0 = si.boundary_data(LEVEL, 21)
+    b = si.rhs(LEVEL, RHS_SEED)
+    want = O.smooth(pr.A, N, pr.Ls, pr.Dinv_s, x0.copy(), b, 2)
+    scale = np.abs(want).max()
+    out = {"sweeps_vs_oracle": {}, "tolerance": {"F64": 1e-12, "MIXED": "1e-5 relative per sweep"}}
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    sol = {}
+    for name, prec in [("MIXED", g.MIXED), ("F64", g.F64)]:
+        t = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=prec,
+                  stencil=g.STENCIL_ON_THE_FLY, values=g.VALUES_ON_THE_FLY, device=torch.cuda.current_device())
+        t.import_surrogate(pr.coefs)
+        xd = torch.tensor(x0, dtype=torch.float64, device="cuda")
+        t.smooth(xd, bd, 2)
+        out["sweeps_vs_oracle"][f"{name}_after_2_sweeps"] = float(np.abs(xd.cpu().numpy() - want).max() / scale)
+        x = torch.zeros(g.num_nodes(LEVEL), dtype=torch.float64, device="cuda")
+        it, rel, ok = t.solve(x, bd, g.PCG, 1e-8, 2000)
+        sol[name] = (it, rel, bool(ok), x.cpu().numpy())
+        t.close()
+    ref = sol["F64"][3]
+    out["pcg_to_1e-8"] = {nm: {"iterations": v[0], "relative_residual": v[1], "converged": v[2]}
+                          for nm, v in sol.items()}
+    out["pcg_MIXED_vs_F64_solution"] = float(np.abs(sol["MIXED"][3] - ref).max() / np.abs(ref).max())
+    return out
+
+
+def single_workload(args, g, torch, rank, world, dist, local):
+    """The default line: the matrix-free MIXED sweep of the level-7 tet (the
+    operator assembled and the surrogates evaluated on the fly), its roofline
+    and depth bound, the other precisions and the stored variants as labelled
+    extras, then the level-9, batch and error keys."""
+    W = max(3, args.warmup)
+    K = max(1, args.steps)
+    P = si.macro_tet(TET_SEED)
+    mf = dict(stencil=g.STENCIL_ON_THE_FLY, values=g.VALUES_ON_THE_FLY)
+    t = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=g.MIXED, device=local, **mf)
+    nn = g.num_nodes(LEVEL)
+    b_h = si.rhs(LEVEL, RHS_SEED)
+    b = torch.tensor(b_h, dtype=torch.float64, device="cuda")
+    x = torch.zeros(nn, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(W):
+        t.smooth(x, b, 1)
+    torch.cuda.synchronize()
+    t.profile(True)
+    t.profile_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms_steps = time_steps(t, x, b, K, flush, stream, torch)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(ms_steps)
+    kms, launches = t.profile_read()
+    t.profile(False)
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_rate(world, interior(LEVEL), K, total_ms)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    xh = np.zeros(nn)
+    t.smooth_host(xh, b_h, 1)
+    E = max(3, min(K, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(E):
+        t.smooth_host(xh, b_h, 1)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = world * interior(LEVEL) * E / e2e_s
+
+    # roofline of the dominant kernel (HBM) and the sweep's depth bound
+    alg = algorithmic(LEVEL, DEG)
+    names = ["residual", "forward", "backward"]
+    per_launch = {nm: kms[i] / K for i, nm in enumerate(names)}
+    dom = max(["forward", "backward"], key=lambda nm: per_launch[nm])
+    hbm, src = peaks()
+    achieved = alg[dom]["bytes"] / (per_launch[dom] / 1e3) / 1e9
+    sm_mhz = clk["sm_mhz"] or 2070.0
+    levels = 3 * 2 ** LEVEL - 11
+    depth = depth_bound(g, levels, 128, sm_mhz)  # slab CTAs: four compute warps per level step
+    hbm_us = 1e6 * sum(alg[nm]["bytes"] for nm in names) / (hbm * 1e9)
+    sweep_us = 1e3 * total_ms / K
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": profiled_traffic(dom), "kernel": f"{dom}_kernel", "peak_source": src,
+            "algorithmic_bytes": alg[dom]["bytes"],
+            "kernel_ms_per_launch": {nm: round(v, 5) for nm, v in per_launch.items()},
+            "sweep": {"algorithmic_bytes": sum(alg[nm]["bytes"] for nm in names), "hbm_time_us": round(hbm_us, 2),
+                      "depth_time_us": depth["us_per_sweep"], "measured_us": round(sweep_us, 2),
+                      "frac_of_binding_bound": round(max(hbm_us, depth["us_per_sweep"]) / sweep_us, 4),
+                      "binding": "depth" if depth["us_per_sweep"] > hbm_us else "hbm"},
+            "depth": dict(depth, cycles_per_level_measured=round(
+                (per_launch["forward"] + per_launch["backward"]) / 2 * 1e-3 / levels * sm_mhz * 1e6))}
+
+    # the same sweep in the other precisions (matrix-free), and the stored variants as labelled extras
+    Kp = max(3, min(K, 50))
+    prec = {"F32": sweep_variant(g, torch, P, flush, stream, W, Kp, prec=g.F32, **mf),
+            "F64": sweep_variant(g, torch, P, flush, stream, W, Kp, prec=g.F64, **mf)}
+    nint = interior(LEVEL)
+    stored = {
+        "MIXED_stored_stencils": dict(sweep_variant(g, torch, P, flush, stream, W, Kp, prec=g.MIXED,
+                                                    stencil=g.STENCIL_STORED, values=g.VALUES_ON_THE_FLY),
+                                      stored_bytes_per_dof=112, note="14 FP64 coefficients per point, read by "
+                                                                     "the residual: 132 instead of 28 B/DoF"),
+        "F64_tabulated_values": dict(sweep_variant(g, torch, P, flush, stream, W, Kp, prec=g.F64,
+                                                   stencil=g.STENCIL_ON_THE_FLY, values=g.VALUES_TABULATED),
+                                     stored_bytes_per_dof=128, note="16 FP64 surrogate values per point, read by "
+                                                                    "the substitutions instead of evaluated"),
+    }
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "level": LEVEL, "degree": DEG, "precision": "MIXED",
+                       "operator": "assembled on the fly", "surrogates": "evaluated on the fly",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nn * 8,
+                    "d2h_bytes_per_step": nn * 8},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "other_precisions": prec,
+            "stored_variants": stored,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]}}
+    t.close()
+    if rank == 0 and not args.no_extras:
+        line["level9"] = level9_workload(args, g, torch, compact=True)
+        line["batch"] = batch_workload(args, g, torch, compact=True)
+        line["error"] = error_report(g, torch, P)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(8)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,6 +933,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="default line without the level9/batch/error keys")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary"])
     ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
     ap.add_argument("--requests", type=int, default=300)
@@ -683,123 +969,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    W = max(3, args.warmup)
-    K = max(1, args.steps)
-
-    P = si.macro_tet(TET_SEED)
-    t = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=g.MIXED, device=local)
-    nn = g.num_nodes(LEVEL)
-    b_h = si.rhs(LEVEL, RHS_SEED)
-    b = torch.tensor(b_h, dtype=torch.float64, device="cuda")
-    x = torch.zeros(nn, dtype=torch.float64, device="cuda")
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    for _ in range(W):
-        t.smooth(x, b, 1)
-    torch.cuda.synchronize()
-    t.profile(True)
-    t.profile_read()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    for k in range(K):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        t.smooth(x, b, 1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms_steps = [a.elapsed_time(bb) for a, bb in ev]
-    total_ms = sum(ms_steps)
-    kms, launches = t.profile_read()
-    t.profile(False)
-    total_ms = max_over_ranks(total_ms, dist, "cuda")
-    value = whole_job_rate(world, interior(LEVEL), K, total_ms)
-
-    # end to end through the host-buffer entry point (copies inside the timed region)
-    xh = np.zeros(nn)
-    t.smooth_host(xh, b_h, 1)
-    E = max(3, min(K, 50))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(E):
-        t.smooth_host(xh, b_h, 1)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * interior(LEVEL) * E / e2e_s
-
-    # roofline of the dominant kernel
-    alg = algorithmic(LEVEL, DEG)
-    names = ["residual", "forward", "backward"]
-    per_launch = {nm: kms[i] / K for i, nm in enumerate(names)}
-    dom = max(names, key=lambda nm: per_launch[nm])
-    hbm, src = peaks()
-    if dom == "residual":
-        achieved = alg[dom]["flops"] / (per_launch[dom] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "residual_kernel (FP64)",
-                "peak_source": "FP64 unit counts x max clock"}
-    else:
-        achieved = alg[dom]["bytes"] / (per_launch[dom] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": profiled_traffic(dom), "kernel": f"{dom}_kernel", "peak_source": src,
-                "algorithmic_bytes": alg[dom]["bytes"]}
-    roof["kernel_ms_per_launch"] = {nm: round(v, 5) for nm, v in per_launch.items()}
-    # The substitutions are bound by their dependency depth (3N - 11
-    # hyperplanes, each a step of the slab on the critical path), not by HBM:
-    # report the measured time per hyperplane beside the HBM fraction.
-    levels = 3 * 2 ** LEVEL - 11
-    sm_mhz = clk["sm_mhz"] or 2070.0
-    sub_ms = (per_launch["forward"] + per_launch["backward"]) / 2
-    depth = {"levels_per_substitution": levels, "us_per_level": round(1e3 * sub_ms / levels, 4),
-             "cycles_per_level": round(sub_ms * 1e-3 / levels * sm_mhz * 1e6),
-             "hbm_time_us_per_substitution": round(1e6 * alg["backward"]["bytes"] / (hbm * 1e9), 2)}
-
-    # the same sweep in the other two precisions (timed the same way, after
-    # the headline measurement)
-    prec = {}
-    # F64 reads its surrogate values from tables by default (ilu_opts.values);
-    # F64_on_the_fly evaluates the row polynomials at every point as Alg. 2 does
-    for name, pp, dt, vals in [("F32", g.F32, torch.float32, g.VALUES_AUTO),
-                               ("F64", g.F64, torch.float64, g.VALUES_AUTO),
-                               ("F64_on_the_fly", g.F64, torch.float64, g.VALUES_ON_THE_FLY)]:
-        tp = g.Tet(P, LEVEL, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=pp, device=local, values=vals)
-        bp = torch.tensor(b_h, dtype=dt, device="cuda")
-        xp = torch.zeros(nn, dtype=dt, device="cuda")
-        tp.smooth(xp, bp, W)
-        Kp = max(3, min(K, 50))
-        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(Kp)]
-        for k in range(Kp):
-            flush.fill_(float(k))
-            evp[k][0].record(stream)
-            tp.smooth(xp, bp, 1)
-            evp[k][1].record(stream)
-        torch.cuda.synchronize()
-        msp = sum(a.elapsed_time(bb) for a, bb in evp) / Kp
-        prec[name] = {"ms_per_step": round(msp, 5), "value": interior(LEVEL) / (msp / 1e3)}
-        tp.close()
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "level": LEVEL, "degree": DEG, "precision": "MIXED",
-                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nn * 8,
-                    "d2h_bytes_per_step": nn * 8},
-            "gpu_launches": int(launches),
-            "roofline": roof,
-            "depth": depth,
-            "other_precisions": prec,
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
-                       "samples": clk["samples"]}}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(8)
+    line = single_workload(args, g, torch, rank, world, dist, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

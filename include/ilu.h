@@ -314,20 +314,33 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 /* The row schedule the packed kernels (ILU_KERNEL_PACKED) follow for one
  * substitution at a level (the same for every tet of that level), for
  * inspection and testing.  lanes: 0 for the kernels' own lane count, else
- * 1..511 for the same construction on that many lanes.  *nsteps and
- * *lanes_out receive its size; with entries (8 ints per interior row: step of
- * its first point, n | y << 10 | z << 20 with n its point count, grid index
- * of its point x = 0, row id, three producer codes, 0) and lane_off (lanes +
- * 1 ints) non-null they receive the schedule, rows grouped by lane in step
- * order.  A producer code has its mode in bits 30-31: 0 no such interior row;
- * 1 ring: the producer's lane in bits 0-8 and, in bits 9-13, the step
- * distance k0 of the first value the consumer reads; 2 global: bits 0-29 the
- * grid index of the producer row's point x = 0.  Forward producers of row
- * (y, z): (y-1, z), (y, z-1), (y+1, z-1); backward: (y+1, z), (y, z+1),
- * (y-1, z+1).  Host-only; the paper sweeps lexicographically on one core,
- * this arrangement is the library's.  ILU_EINVAL for a level outside 2..8. */
-ilu_status ilu_packed_schedule(int level, int forward, int lanes, int *nsteps, int *lanes_out, int *entries,
-                               int *lane_off);
+ * 1..511 for the same construction on that many lanes; quantum: 0 for the
+ * kernels' start quantum at that level (1 up to level 6, 2 at 7, 4 at 8),
+ * else 1, 2 or 4.  *nsteps and *lanes_out receive its size; with entries and
+ * lane_off (lanes + 1 ints) non-null they receive the schedule, rows grouped
+ * by lane in step order, 8 ints per interior row, in the pass's own steps:
+ *   [0] sw | (lo - sw) << 16: the row's switch step sw (quantum - 1 modulo
+ *       the quantum; the lane computes no point there) and the step lo of
+ *       its first point;
+ *   [1] n | y << 10 | z << 20, n the row's point count;
+ *   [2] R0 | R1 << 14 | far << 28 and [3] R2 | row id << 14: R_j the word of
+ *       the kernels' shared ring (384 + 8 words a step) holding producer j's
+ *       value read at the first step of the 8-step block holding sw (word 384,
+ *       never written, if the producer row does not exist or is read from
+ *       global memory), bit j of far set for the latter;
+ *   [4] the row coordinate (2x - (N - y - z)) / (2N) of step sw's point
+ *       (float bits; x = 0 forward, n + lo - sw backward);
+ *   [5..7] the producer codes: mode in bits 30-31 (0 no such interior row,
+ *       1 read from the ring, 2 read from global memory), the producer's lane
+ *       in bits 0-8, and in bits 9-29 the step distance k0 of the first value
+ *       the consumer reads (the producer's value at step tau + 1 - k0 is its
+ *       second value at step tau).
+ * Forward producers of row (y, z): (y-1, z), (y, z-1), (y+1, z-1); backward:
+ * (y+1, z), (y, z+1), (y-1, z+1).  Host-only; the paper sweeps
+ * lexicographically on one core, this arrangement is the library's.
+ * ILU_EINVAL for a level outside 2..8 or a bad lanes or quantum. */
+ilu_status ilu_packed_schedule(int level, int forward, int lanes, int quantum, int *nsteps, int *lanes_out,
+                               int *entries, int *lane_off);
 
 /* Split n macro-tetrahedra over nranks GPUs for a batch or a request stream
  * on several devices: cost[i] (host, finite, >= 0; e.g. interior points x

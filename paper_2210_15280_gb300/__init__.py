@@ -131,7 +131,7 @@ def lib():
         L.ilu_profile_enable.argtypes = [vp, i]
         L.ilu_profile_read.argtypes = [vp, vp, P(ctypes.c_longlong)]
         L.ilu_num_nodes.argtypes = [i]; L.ilu_num_nodes.restype = sz
-        L.ilu_packed_schedule.argtypes = [i, i, i, vp, vp, vp, vp]
+        L.ilu_packed_schedule.argtypes = [i, i, i, i, vp, vp, vp, vp]
         L.ilu_partition.argtypes = [i, vp, i, vp, vp]
         L.ilu_step_floor.argtypes = [i, i, i, vp]
         L.ilu_num_interior.argtypes = [i]; L.ilu_num_interior.restype = sz
@@ -170,18 +170,18 @@ def partition(costs, nranks):
     return rank_of, load
 
 
-def packed_schedule(level, forward=True, lanes=0):
+def packed_schedule(level, forward=True, lanes=0, quantum=0):
     """Row schedule of the packed kernels for one substitution at `level`
     (ilu_packed_schedule): (nsteps, lanes, entries[rows, 8], lane_off)."""
     ns, ln = ctypes.c_int(0), ctypes.c_int(0)
-    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), ctypes.byref(ns), ctypes.byref(ln),
-                                     None, None))
+    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), int(quantum), ctypes.byref(ns),
+                                     ctypes.byref(ln), None, None))
     n = 2 ** int(level)
     rows = (n - 3) * (n - 2) // 2 if n >= 4 else 0
     ent = np.zeros((rows, 8), dtype=np.int32)
     off = np.zeros(ln.value + 1, dtype=np.int32)
-    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), ctypes.byref(ns), ctypes.byref(ln),
-                                     _ptr(ent), _ptr(off)))
+    _check(lib().ilu_packed_schedule(int(level), int(bool(forward)), int(lanes), int(quantum), ctypes.byref(ns),
+                                     ctypes.byref(ln), _ptr(ent), _ptr(off)))
     return ns.value, ln.value, ent, off
 
 

@@ -6,7 +6,8 @@
 //   3. the substitutions, as independent branches of the pass so that their
 //      kernels run concurrently:
 //      - tets whose handles use the packed kernels: one launch per row-table
-//        layout, a CTA per tet holding its forward and backward substitution,
+//        layout and schedule quantum (level 7 and level 8 schedules differ),
+//        a CTA per tet holding its forward and backward substitution,
 //        tets ordered by their step count, longest first (the CTAs of the
 //        longest tets start first, the short ones fill in behind them); no
 //        CTA waits on another;
@@ -69,10 +70,11 @@ struct Group {
   cudaEvent_t done = nullptr;
 };
 
-// Tets on the packed kernels with the same row-table layout: one launch, a
-// CTA per tet, longest tets first (their CTAs start first).
+// Tets on the packed kernels with the same row-table layout and schedule
+// quantum: one launch, a CTA per tet, longest tets first (their CTAs start
+// first).
 struct PackedGroup {
-  int dxp = 0, reg = 0;
+  int dxp = 0, reg = 0, q = 1;
   bool v1 = false;
   std::vector<int> members;  // tet indices, most steps first
   PackedLaunch pl = {};
@@ -170,11 +172,11 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   // rows in registers, rows in shared memory, tabulated values
   auto cls = [](const TetView &v) { return v.reg >= 0 ? 1 : (v.reg == kWaveTabulated ? 2 : 0); };
   std::map<std::tuple<int, int, int>, int> key;
-  std::map<int, int> pkey;  // packed tets by table layout
+  std::map<std::pair<int, int>, int> pkey;  // packed tets by table layout and start quantum
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
     if (v.packed) {
-      pkey.emplace(v.rstride, 0);
+      pkey.emplace(std::make_pair(v.rstride, v.packed_q), 0);
       continue;
     }
     const auto k = std::make_tuple(-v.N, cls(v), v.rstride);  // largest levels first
@@ -193,8 +195,9 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
     if (v.packed) {
-      PackedGroup &pg = b->pgroups[pkey[v.rstride]];
+      PackedGroup &pg = b->pgroups[pkey[std::make_pair(v.rstride, v.packed_q)]];
       pg.dxp = v.rstride;
+      pg.q = v.packed_q;
       pg.reg = v.dx <= 3 ? 3 : 6;  // the degree of the tets' packed tables (zero padded, as their own launches)
       pg.v1 = pg.v1 || v.dev->bnd != nullptr;
       pg.members.push_back(i);
@@ -338,6 +341,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       L.order = b->d_porder + at;
       L.ntets = (int)pg.members.size();
       L.reg = pg.reg;
+      L.q = pg.q;
       L.v1 = pg.v1;
       at += pg.members.size();
       BK(cudaStreamCreateWithFlags(&pg.st, cudaStreamNonBlocking), "cudaStreamCreate");

@@ -208,7 +208,8 @@ struct PackedLaunch {
   const DevTet *tets;
   const int *order;
   int ntets;
-  int reg;
+  int reg;  // degree of the row tables (3 or 6)
+  int q;    // the schedules' start quantum (1, 2 or 4; the same for every tet of the launch)
   bool v1;
 };
 size_t packed_smem_bytes(int reg);
@@ -233,6 +234,7 @@ struct TetView {
   bool failed;
   bool packed;  // its substitutions run on the packed kernels (cost: steps of both passes)
   int packed_steps;
+  int packed_q;  // their schedules' start quantum
 };
 bool tet_view(ilu_tet_s *t, TetView *v);
 // partition of one substitution (requested > 0: about that many slabs)

@@ -7,8 +7,9 @@
 // and then the backward substitution
 //     w^p <- D~^-1(p) w^p - sum_{d in D_l, p-d interior} L~^{p-d}_d w^{p-d},
 // walking the steps of the tet's host-computed row schedule (packed.h): at
-// step tau every lane computes one point of the row it owns (or idles), then
-// the CTA meets at a block barrier.  No CTA waits on another.  Everything the
+// step tau every lane computes one point of the row it owns (or writes 0),
+// and every Q steps the CTA meets at a block barrier.  No CTA waits on
+// another.  Everything the
 // passes read and write lies in the tet's step-major packed array, where the
 // lanes of a warp touch consecutive words at every step; packed_io_kernel
 // moves vectors between the lexicographic grid and that array (the residual
@@ -20,13 +21,14 @@
 //              its own row, the producer values carried from the last step;
 //   ring       its results of the last kPackedRing steps (shared memory);
 //              consumers read producer values there by (step, lane);
-//   queue      the input of the next kPackedPre steps, plus the values of
-//              producer rows that ran too far ahead for the ring, read back
-//              from the packed array -- filled by cp.async;
+//   queue      the values of producer rows that ran too far ahead for the
+//              ring, read back from the packed array kPackedPre steps ahead
+//              -- filled by cp.async;
 //   stage      the next row's coefficients and the schedule entry after it,
 //              filled by cp.async while the current row runs.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -36,7 +38,11 @@ namespace ilu {
 namespace {
 
 constexpr int LN = kPackedLanes, RG = kPackedRing, QS = kPackedQueue, PD = kPackedPre;
+constexpr int RW = kPackedRingRow;         // words per ring row; column LN is never written (reads 0)
+constexpr int RR = RG + kPackedBlock;      // ring rows: RG, then a mirror of rows 0 .. kPackedBlock - 1
 static_assert((RG & (RG - 1)) == 0 && (QS & (QS - 1)) == 0, "ring and queue sizes are powers of two");
+static_assert(QS == kPackedBlock, "a step's queue slot is its index in the unrolled block");
+static_assert(RG % kPackedBlock == 0, "blocks tile the ring");
 static_assert(PD < QS, "the entry read at a step must not be the one being refilled");
 static_assert(RG - 1 >= PD + 1, "ring and global reads must cover every producer distance");
 
@@ -72,281 +78,332 @@ __device__ __forceinline__ int pmode(int code) { return (code >> 30) & 3; }
 
 // One substitution of one tet on one CTA.
 //
-// Lane state: the current row (first step, points, the centred-coordinate
-// offset N - y - z, producer codes), and per producer the ring index of the
-// value it reads next and the value it read last (a consumer's first value
-// at a step is its second value of the step before, so one ring read or
-// queue entry per producer and step suffices); the next row's schedule entry
-// (staged).  A lane switches to its next row on the idle step before the
-// row's first point; the row's coefficients are read from the stage at the
-// first point, and the stage is refilled for the row after at the end of
-// that step.  Steps run in blocks of four: at the start of block g each lane
-// loads its inputs of block g + 1 (one 16-byte load), and at the end of
-// block g it stores the block's four results over their inputs.
-template <bool FWD, int DX, bool V1>
+// Lane state: the current row (its points' steps [lo, lo + n), the ring word
+// of each producer's read at the current block's first step, which
+// producers come through the queue), the value each producer gave at the
+// last step (a consumer's first value at a step is its second value of the
+// step before, so one read per producer and step suffices), the lane's own
+// value of the last step, the row coordinate t of the step's point (advanced
+// by h per step; every value is a small dyadic fraction, so the sums are
+// exact), and the next row's schedule entry.  Two per-lane events change it:
+// kPackedPre steps before the next row's switch step the prefetch cursor
+// moves to that row and the copies of its coefficients and of the entry
+// after it are issued; on the switch step the row becomes current
+// (coefficients from the stage, the entry after it from `sent`).  Switch
+// steps are Q - 1 (mod Q), so only those unrolled positions test for events.
+//
+// The CTA meets at a block barrier after every step Q - 1 (mod Q): the
+// schedule keeps every producer value at least Q + 1 steps ahead of the step
+// that reads it and reads the ring only up to kPackedRing + 1 - Q steps back,
+// so a value is visible when read and not yet overwritten, however far apart
+// the lanes are between two barriers.  A lane's own stage and `sent` are
+// refilled only after the barrier that follows the switch step reading them.
+//
+// Steps with no point of the lane write 0.  The schedule leaves such a step
+// before and after every row, in both passes, and these are exactly the
+// steps at which a consumer reads a producer's missing neighbour (x = 0, or
+// one past the producer row's end); a producer row that does not exist is
+// read from ring column kPackedLanes, which is never written.  So the point
+// arithmetic needs no masks.
+//
+// The loop runs in blocks of kPackedBlock steps, unrolled, so that ring rows
+// and queue slots are compile-time offsets from per-block bases: ring row
+// (tau & (RG-1)) holds step tau's results, and the first kPackedBlock rows
+// are mirrored after row RG - 1 so that a producer's reads within a block
+// never wrap.  Inputs are read and results written four steps at a time (one
+// 16-byte block per lane).
+template <bool FWD, int DX, bool V1, int Q>
 __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem) {
   constexpr int SF2 = 4 * (DX + 1);  // float2 of a staged row: coefficient k of the four function pairs
-  float *ring = reinterpret_cast<float *>(smem);                 // [RG][LN]
-  float4 *q = reinterpret_cast<float4 *>(ring + RG * LN);        // [QS][LN] far producer values (.y .z .w)
+  float *ring = reinterpret_cast<float *>(smem);                 // [RR][RW]
+  float4 *q = reinterpret_cast<float4 *>(ring + RR * RW);        // [QS][LN] far producer values (.y .z .w)
   int4 *sent = reinterpret_cast<int4 *>(q + QS * LN);            // [LN][2]
   float2 *stage = reinterpret_cast<float2 *>(sent + 2 * LN);     // [LN][SF2]
   const int lane = threadIdx.x;
   const int N = t.N;
   const int4 *ent = FWD ? t.pk.ent_f : t.pk.ent_b;  // entry e at ent[2e], ent[2e + 1]
   const int *off = t.pk.off;
-  const int T = t.pk.nsteps;  // a multiple of 4
+  const int T = t.pk.nsteps;  // a multiple of kPackedBlock
   const float2 *tab = reinterpret_cast<const float2 *>(FWD ? t.pkF : t.pkB);
   float *pw = t.pk.pw;  // packed array; backward step tau works on forward step T - 1 - tau
   const float hh = (float)(0.5 * t.h);
   float2 *my_stage = stage + lane * SF2;
 
+  // ring rows of steps before 0 read as 0; column LN stays 0 for good
+  {
+    float4 *r4 = reinterpret_cast<float4 *>(ring);
+    for (int i = lane; i < RR * RW / 4; i += LN) r4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+
   const int e_end = off[lane + 1];
-  int e_cur = off[lane] - 1;
-  bool has_nxt = e_cur + 1 < e_end, stage_pending = false;
-  int4 na = make_int4(0, 0, 0, 0), nb = make_int4(0, 0, 0, 0);  // the next row's entry
-  // current row: none yet (its step range is empty)
-  int c_start = -8, c_n = 0, c_K = 0, c_p0 = 0, c_p1 = 0, c_p2 = 0, c_far = 0;
-  int c_y = 0, c_z = 0;  // read by boundary variant V1 only
-  int s0 = lane, s1 = lane, s2 = lane;          // ring index of each producer's next value
-  float cv0 = 0.f, cv1 = 0.f, cv2 = 0.f;        // each producer's value of the last step
-  float v1 = 0.f;                               // this row's previous value
+  int e_nx = off[lane];  // index of the next row's entry
+  int4 nxa = make_int4(0, 0, 0, 0), nxb = make_int4(0, 0, 0, 0);  // the next row's entry
+  int ev = INT_MAX;  // the next row's switch step (its cursor event is kPackedPre steps earlier)
+  if (e_nx < e_end) {
+    nxa = ent[2 * e_nx];
+    nxb = ent[2 * e_nx + 1];
+    ev = nxa.x & 0xffff;
+  }
+
+  // position in the packed array of this pass's step s; the 16-byte block of
+  // this lane holding steps 4g..4g+3 (backward: positions T-1-4g .. T-4-4g,
+  // the block's elements in reverse order)
+  auto ppos = [&](int s) { return FWD ? s : T - 1 - s; };
+  auto block = [&](int g) {
+    return reinterpret_cast<float4 *>(pw) + (size_t)(FWD ? g : (T >> 2) - 1 - g) * LN + lane;
+  };
+
+  // prefetch cursor: the far producers of the row this lane works on
+  // kPackedPre steps ahead (word offsets into pw of their next values)
+  int pgm = 0, pf_end = -1, o0 = 0, o1 = 0, o2 = 0;
+  // the cursor moves to the next row at step tau2 = its switch step: its far
+  // producers, and the copies of its coefficients and of the entry after it
+  auto cursor = [&](int tau2) {
+    pgm = (nxa.z >> 28) & 7;
+    const int lo = (nxa.x & 0xffff) + (nxa.x >> 16);
+    pf_end = lo + (nxa.y & 1023) - 1;
+    auto pos0 = [&](int code) {  // the value read at step tau2
+      return (int)packed_index(ppos(tau2 - ((code >> 9) & 0x1fffff) + 1), code & 511);
+    };
+    if (pgm) {
+      o0 = pos0(nxb.y);
+      o1 = pos0(nxb.z);
+      o2 = pos0(nxb.w);
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)(nxa.w >> 14) * SF2);
+    float4 *dst = reinterpret_cast<float4 *>(my_stage);
+#pragma unroll
+    for (int i = 0; i < SF2 / 2; ++i) cpa16(dst + i, src + i);
+    if (e_nx + 1 < e_end) {
+      cpa16(&sent[2 * lane], &ent[2 * (e_nx + 1)]);
+      cpa16(&sent[2 * lane + 1], &ent[2 * (e_nx + 1) + 1]);
+    }
+  };
+  // the next value of a far producer (position offset o, one step on)
+  auto next_pos = [&](int &o) {
+    if (FWD) o += (o & 3) == 3 ? 4 * LN - 3 : 1;
+    else o -= (o & 3) == 0 ? 4 * LN - 3 : 1;
+  };
+  auto prefetch = [&](int tau2) {  // one commit group per step
+    if (pgm && tau2 <= pf_end) {
+      float *d = reinterpret_cast<float *>(q + (tau2 & (QS - 1)) * LN + lane);
+      if (pgm & 1) cpa<4>(d + 1, pw + o0);
+      if (pgm & 2) cpa<4>(d + 2, pw + o1);
+      if (pgm & 4) cpa<4>(d + 3, pw + o2);
+      next_pos(o0);
+      next_pos(o1);
+      next_pos(o2);
+    }
+    cpa_commit();
+  };
+#pragma unroll 1
+  for (int s = 0; s < PD; ++s) {
+    if (s == ev) cursor(s);
+    prefetch(s);
+  }
+
+  // current row
+  int lo = 0, cn = 0, c_y = 0, c_z = 0;
+  int gm = 0;                       // bit j: producer j comes through the queue
+  int B0 = LN, B1 = LN, B2 = LN;    // ring word of each producer's read at the block's first step
+  float cv0 = 0.f, cv1 = 0.f, cv2 = 0.f;  // each producer's value of the last step
+  float v1 = 0.f;                         // this lane's value of the last step
+  float2 t2 = make_float2(0.f, 0.f);
+  const float2 dt2 = FWD ? make_float2(2.f * hh, 2.f * hh) : make_float2(-2.f * hh, -2.f * hh);
+  const float2 one2 = make_float2(1.f, 1.f);
   float2 c[4][DX + 1];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int k = 0; k <= DX; ++k) c[p][k] = make_float2(0.f, 0.f);
 
-  auto stage_rows = [&](int rid, int e_after) {  // coefficients of row rid, entry e_after
-    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)rid * SF2);
-    float4 *dst = reinterpret_cast<float4 *>(my_stage);
+  auto switch_row = [&]() {  // on the next row's switch step
+    lo = (nxa.x & 0xffff) + (nxa.x >> 16);
+    cn = nxa.y & 1023;
+    c_y = (nxa.y >> 10) & 1023;
+    c_z = nxa.y >> 20;
+    B0 = nxa.z & 0x3fff;
+    B1 = (nxa.z >> 14) & 0x3fff;
+    B2 = nxa.w & 0x3fff;
+    gm = (nxa.z >> 28) & 7;
+    const float tt = __int_as_float(nxb.x);
+    t2 = make_float2(tt, tt);
+    const float4 *sv = reinterpret_cast<const float4 *>(my_stage);
 #pragma unroll
-    for (int i = 0; i < SF2 / 2; ++i) cpa16(dst + i, src + i);
-    if (e_after < e_end) {
-      cpa16(&sent[2 * lane], &ent[2 * e_after]);
-      cpa16(&sent[2 * lane + 1], &ent[2 * e_after + 1]);
+    for (int k = 0; k <= DX; ++k) {
+      const float4 a = sv[2 * k], b = sv[2 * k + 1];
+      c[0][k] = make_float2(a.x, a.y);
+      c[1][k] = make_float2(a.z, a.w);
+      c[2][k] = make_float2(b.x, b.y);
+      c[3][k] = make_float2(b.z, b.w);
+    }
+    ++e_nx;
+    ev = INT_MAX;
+    if (e_nx < e_end) {
+      nxa = sent[2 * lane];
+      nxb = sent[2 * lane + 1];
+      ev = nxa.x & 0xffff;
     }
   };
-  if (has_nxt) {
-    na = ent[2 * (e_cur + 1)];
-    nb = ent[2 * (e_cur + 1) + 1];
-    stage_rows(na.w, e_cur + 2);
-  }
-  cpa_commit();
 
-  // Position in the packed array of this pass's step s, and the 16-byte
-  // block of this lane holding steps 4g..4g+3 (backward: positions
-  // T-1-4g .. T-4-4g, the block's elements in reverse order).
-  auto ppos = [&](int s) { return FWD ? s : T - 1 - s; };
-  auto block = [&](int g) {
-    return reinterpret_cast<float4 *>(pw) + (size_t)(FWD ? g : (T >> 2) - 1 - g) * LN + lane;
-  };
-  // far producer values of the point this lane works on at step tau2; one
-  // commit group per step (a producer's second value of step tau2 was written
-  // at tau2 - k0 + 1 >= tau2 - kPackedPre - ... well before this copy)
-  auto prefetch = [&](int tau2) {
-    const bool uc = tau2 <= c_start + c_n - 1;
-    const bool un = !uc && has_nxt && tau2 >= na.x - 1;
-    if ((uc && c_far) || (un && nb.w)) {
-      const int p0 = uc ? c_p0 : nb.x, p1 = uc ? c_p1 : nb.y, p2 = uc ? c_p2 : nb.z;
-      float *d = reinterpret_cast<float *>(q + (tau2 & (QS - 1)) * LN + lane);
-      if (pmode(p0) == kProdGlobal)
-        cpa<4>(d + 1, pw + packed_index(ppos(tau2 - ((p0 >> 9) & 0x1fffff) + 1), p0 & 511));
-      if (pmode(p1) == kProdGlobal)
-        cpa<4>(d + 2, pw + packed_index(ppos(tau2 - ((p1 >> 9) & 0x1fffff) + 1), p1 & 511));
-      if (pmode(p2) == kProdGlobal)
-        cpa<4>(d + 3, pw + packed_index(ppos(tau2 - ((p2 >> 9) & 0x1fffff) + 1), p2 & 511));
-    }
-    cpa_commit();
-  };
-#pragma unroll 1
-  for (int s = 0; s < PD; ++s) prefetch(s);
-
-  // ring index of a producer's value at step tau + 1 - k0 (its second value at tau)
-  auto ring_start = [&](int code, int tau) {
-    return pmode(code) == kProdRing ? ((tau - ((code >> 9) & 31) + 1) & (RG - 1)) * LN + (code & 511) : lane;
-  };
-
-  // one step: the switch, the far prefetch, the point; input r (forward) or
-  // the forward result (backward); returns this lane's result (0 if idle)
-  auto step = [&](int tau, float in) -> float {
+  // one step (J = tau & (kPackedBlock - 1), a constant after unrolling): the
+  // events, the far prefetch, the point; input r (forward) or the forward
+  // result (backward); returns this lane's result (0 without a point)
+  auto step = [&](int tau, int J, bool mir, int wb, float in) -> float {
     cpa_wait<PD - 1>();  // the far values of step tau are in
-    if (has_nxt && tau == na.x - 1) {  // switch to the next row (its idle step)
-      ++e_cur;
-      c_start = na.x;
-      c_n = na.y & 1023;
-      c_y = (na.y >> 10) & 1023;
-      c_z = na.y >> 20;
-      c_K = N - c_y - c_z;
-      c_p0 = nb.x;
-      c_p1 = nb.y;
-      c_p2 = nb.z;
-      c_far = nb.w;
-      s0 = ring_start(c_p0, tau);
-      s1 = ring_start(c_p1, tau);
-      s2 = ring_start(c_p2, tau);
-      has_nxt = e_cur + 1 < e_end;
-      if (has_nxt) {
-        na = sent[2 * lane];
-        nb = sent[2 * lane + 1];
-      }
-      stage_pending = true;
-    }
-    const bool first = stage_pending && tau == c_start;
-    if (first) {  // the row's coefficients from the stage
-      const float4 *sv = reinterpret_cast<const float4 *>(my_stage);
-#pragma unroll
-      for (int k = 0; k <= DX; ++k) {
-        const float4 a = sv[2 * k], b = sv[2 * k + 1];
-        c[0][k] = make_float2(a.x, a.y);
-        c[1][k] = make_float2(a.z, a.w);
-        c[2][k] = make_float2(b.x, b.y);
-        c[3][k] = make_float2(b.z, b.w);
-      }
-    }
+    if ((J & (Q - 1)) == Q - 1 && tau == ev) switch_row();
+    if (((J + PD) & (Q - 1)) == Q - 1 && tau + PD == ev) cursor(tau + PD);
     prefetch(tau + PD);
-    float out = 0.f;
-    if (tau >= c_start - 1 && tau <= c_start + c_n - 1) {
-      const float4 qv = q[(tau & (QS - 1)) * LN + lane];
-      // each producer's second value of this step: ring, queue or none
-      const float r0 = ring[s0], r1 = ring[s1], r2 = ring[s2];
-      const float b0 = pmode(c_p0) == kProdRing ? r0 : (pmode(c_p0) == kProdGlobal ? qv.y : 0.f);
-      const float b1 = pmode(c_p1) == kProdRing ? r1 : (pmode(c_p1) == kProdGlobal ? qv.z : 0.f);
-      const float b2 = pmode(c_p2) == kProdRing ? r2 : (pmode(c_p2) == kProdGlobal ? qv.w : 0.f);
-      const float a0 = cv0, a1 = cv1, a2 = cv2;  // first values: last step's second values
-      cv0 = b0;
-      cv1 = b1;
-      cv2 = b2;
-      s0 = s0 + LN < RG * LN ? s0 + LN : s0 + LN - RG * LN;
-      s1 = s1 + LN < RG * LN ? s1 + LN : s1 + LN - RG * LN;
-      s2 = s2 + LN < RG * LN ? s2 + LN : s2 + LN - RG * LN;
-      if (tau >= c_start) {
-        const int u = tau - c_start + 1;
-        const int x = FWD ? u : c_n + 1 - u;
-        // the eight row polynomials at the centred row coordinate
-        float L[8];
-        {
-          const float tt = (float)(2 * x - c_K) * hh;
-          const float2 t2 = make_float2(tt, tt);
+    // each producer's second value of this step
+    float r0 = ring[B0 + J * RW], r1 = ring[B1 + J * RW], r2 = ring[B2 + J * RW];
+    if (gm) {
+      const float4 qv = q[J * LN + lane];
+      if (gm & 1) r0 = qv.y;
+      if (gm & 2) r1 = qv.z;
+      if (gm & 4) r2 = qv.w;
+    }
+    const float a0 = cv0, a1 = cv1, a2 = cv2;  // first values: last step's second values
+    cv0 = r0;
+    cv1 = r1;
+    cv2 = r2;
+    // the eight row polynomials at the point's row coordinate
+    float L[8];
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            float2 v = c[p][DX];
+    for (int p = 0; p < 4; ++p) {
+      float2 v = c[p][DX];
 #pragma unroll
-            for (int k = DX - 1; k >= 0; --k) v = ffma2(v, t2, c[p][k]);
-            L[2 * p] = v.x;
-            L[2 * p + 1] = v.y;
-          }
+      for (int k = DX - 1; k >= 0; --k) v = ffma2(v, t2, c[p][k]);
+      L[2 * p] = v.x;
+      L[2 * p + 1] = v.y;
+    }
+    const bool active = (unsigned)(tau - lo) < (unsigned)cn;
+    float acc;
+    if (FWD) {
+      if constexpr (V1) {  // the stored exact L^p_d at a cell-boundary point
+        const float *bndv = reinterpret_cast<const float *>(t.bnd);
+        const int x = tau - lo + 1;
+        if (active && bndv && on_cell_boundary(N, x, c_y, c_z)) {
+          const float *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, c_y, c_z) * 8;
+#pragma unroll
+          for (int d = 0; d < 7; ++d) L[d] = rec[d];
         }
-        const float zero = 0.f;
-        float acc;
-        if (FWD) {
-          if constexpr (V1) {  // the stored exact L^p_d at a cell-boundary point
-            const float *bndv = reinterpret_cast<const float *>(t.bnd);
-            if (bndv && on_cell_boundary(N, x, c_y, c_z)) {
-              const float *rec = bndv + (size_t)bnd_record(t.bnd_off, N, x, c_y, c_z) * 8;
-#pragma unroll
-              for (int d = 0; d < 7; ++d) L[d] = rec[d];
-            }
-          }
-          const bool x2 = x >= 2;
-          const float ws = a0, wse = b0;                  // (x, y-1, z), (x+1, y-1, z): none if y = 1
-          const float wbc = a1, wbe = b1;                 // (x, y, z-1), (x+1, y, z-1): none if z = 1
-          const float wbnw = x2 ? a2 : zero, wbn = b2;    // (x-1, y+1, z-1), (x, y+1, z-1)
-          const float ww = x2 ? v1 : zero;                // (x-1, y, z)
-          acc = in;
-          acc = fmaf(-L[1], ws, acc);
-          acc = fmaf(-L[2], wse, acc);
-          acc = fmaf(-L[3], wbnw, acc);
-          acc = fmaf(-L[4], wbn, acc);
-          acc = fmaf(-L[5], wbc, acc);
-          acc = fmaf(-L[6], wbe, acc);
-          acc = fmaf(-L[0], ww, acc);
-        } else {
-          if constexpr (V1) {  // stored exact 1/D^p at p, L^{p-d}_d where p - d is a cell-boundary point
-            const float *bndv = reinterpret_cast<const float *>(t.bnd);
-            if (bndv) {
-              if (on_cell_boundary(N, x, c_y, c_z))
-                L[0] = bndv[(size_t)bnd_record(t.bnd_off, N, x, c_y, c_z) * 8 + 7];
-#pragma unroll
-              for (int d = 0; d < kNumLower; ++d) {
-                const int qx = x - dir_dx(d), qy = c_y - dir_dy(d), qz = c_z - dir_dz(d);
-                if (in_interior(N, qx, qy, qz) && on_cell_boundary(N, qx, qy, qz))
-                  L[1 + d] = bndv[(size_t)bnd_record(t.bnd_off, N, qx, qy, qz) * 8 + d];
-              }
-            }
-          }
-          const bool inner = u >= 2, x2 = x >= 2;         // x + y + z <= N - 2; x >= 2
-          const float wn = inner ? a0 : zero;             // p - s   = (x, y+1, z)
-          const float wnw = x2 ? b0 : zero;               // p - se  = (x-1, y+1, z)
-          const float wtc = inner ? a1 : zero;            // p - bc  = (x, y, z+1)
-          const float wtw = x2 ? b1 : zero;               // p - be  = (x-1, y, z+1)
-          const float wtse = inner ? a2 : zero;           // p - bnw = (x+1, y-1, z+1): none if y = 1
-          const float wts = b2;                           // p - bn  = (x, y-1, z+1): none if y = 1
-          const float we = inner ? v1 : zero;             // p - w   = (x+1, y, z)
-          acc = L[0] * in;
-          acc = fmaf(-L[2], wn, acc);
-          acc = fmaf(-L[6], wtc, acc);
-          acc = fmaf(-L[4], wtse, acc);
-          acc = fmaf(-L[3], wnw, acc);
-          acc = fmaf(-L[7], wtw, acc);
-          acc = fmaf(-L[5], wts, acc);
-          acc = fmaf(-L[1], we, acc);
-        }
-        ring[(tau & (RG - 1)) * LN + lane] = acc;
-        v1 = acc;
-        out = acc;
       }
+      // producers (x, y-1, z) / (x+1, y-1, z); (x, y, z-1) / (x+1, y, z-1);
+      // (x-1, y+1, z-1) / (x, y+1, z-1); the row's own (x-1, y, z); the
+      // values already held come first, this step's reads last
+      acc = in;
+      acc = fmaf(-L[1], a0, acc);
+      acc = fmaf(-L[5], a1, acc);
+      acc = fmaf(-L[3], a2, acc);
+      acc = fmaf(-L[0], v1, acc);
+      acc = fmaf(-L[2], r0, acc);
+      acc = fmaf(-L[6], r1, acc);
+      acc = fmaf(-L[4], r2, acc);
+    } else {
+      if constexpr (V1) {  // stored exact 1/D^p at p, L^{p-d}_d where p - d is a cell-boundary point
+        const float *bndv = reinterpret_cast<const float *>(t.bnd);
+        const int x = cn + lo - tau;
+        if (active && bndv) {
+          if (on_cell_boundary(N, x, c_y, c_z)) L[0] = bndv[(size_t)bnd_record(t.bnd_off, N, x, c_y, c_z) * 8 + 7];
+#pragma unroll
+          for (int d = 0; d < kNumLower; ++d) {
+            const int qx = x - dir_dx(d), qy = c_y - dir_dy(d), qz = c_z - dir_dz(d);
+            if (in_interior(N, qx, qy, qz) && on_cell_boundary(N, qx, qy, qz))
+              L[1 + d] = bndv[(size_t)bnd_record(t.bnd_off, N, qx, qy, qz) * 8 + d];
+          }
+        }
+      }
+      // p - s = (x, y+1, z) / p - se = (x-1, y+1, z); p - bc = (x, y, z+1) /
+      // p - be = (x-1, y, z+1); p - bnw = (x+1, y-1, z+1) / p - bn = (x, y-1,
+      // z+1); the row's own p - w = (x+1, y, z)
+      acc = L[0] * in;
+      acc = fmaf(-L[2], a0, acc);
+      acc = fmaf(-L[6], a1, acc);
+      acc = fmaf(-L[4], a2, acc);
+      acc = fmaf(-L[1], v1, acc);
+      acc = fmaf(-L[3], r0, acc);
+      acc = fmaf(-L[7], r1, acc);
+      acc = fmaf(-L[5], r2, acc);
     }
-    if (first) {  // the stage is read (its values are in use): refill it for the row after
-      if (has_nxt) stage_rows(na.w, e_cur + 2);
-      stage_pending = false;
-    }
-    __syncthreads();
+    t2 = ffma2(t2, one2, dt2);  // the next point's row coordinate (exact)
+    const float out = active ? acc : 0.f;
+    v1 = out;
+    ring[wb + J * RW] = out;
+    if (mir) ring[(RG + J) * RW + lane] = out;
+    if ((J & (Q - 1)) == Q - 1) __syncthreads();  // every Q steps (producers are at least Q + 1 steps ahead)
     return out;
   };
 
-  const int G = T >> 2;
-  float4 cur = *block(0);  // inputs of block 0 (the residual launch ended before this kernel)
+  const int G = T / kPackedBlock, G4 = T >> 2;
+  float4 cur = *block(0);  // inputs of steps 0..3 (the residual launch ended before this kernel)
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
-    const float4 nxt = g + 1 < G ? *block(g + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 res;
-    if (FWD) {
-      res.x = step(4 * g, cur.x);
-      res.y = step(4 * g + 1, cur.y);
-      res.z = step(4 * g + 2, cur.z);
-      res.w = step(4 * g + 3, cur.w);
-    } else {  // positions descend: the block's last element is this pass's first step
-      res.w = step(4 * g, cur.w);
-      res.z = step(4 * g + 1, cur.z);
-      res.y = step(4 * g + 2, cur.y);
-      res.x = step(4 * g + 3, cur.x);
+    const int tau0 = g * kPackedBlock;
+    const bool mir = (g & (RG / kPackedBlock - 1)) == 0;  // ring rows 0..7: also write their mirror
+    const int wb = (tau0 & (RG - 1)) * RW + lane;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g4 = 2 * g + h;
+      const float4 nxt = g4 + 1 < G4 ? *block(g4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 res;
+      if (FWD) {
+        res.x = step(tau0 + 4 * h, 4 * h, mir, wb, cur.x);
+        res.y = step(tau0 + 4 * h + 1, 4 * h + 1, mir, wb, cur.y);
+        res.z = step(tau0 + 4 * h + 2, 4 * h + 2, mir, wb, cur.z);
+        res.w = step(tau0 + 4 * h + 3, 4 * h + 3, mir, wb, cur.w);
+      } else {  // positions descend: the block's last element is this pass's first step
+        res.w = step(tau0 + 4 * h, 4 * h, mir, wb, cur.w);
+        res.z = step(tau0 + 4 * h + 1, 4 * h + 1, mir, wb, cur.z);
+        res.y = step(tau0 + 4 * h + 2, 4 * h + 2, mir, wb, cur.y);
+        res.x = step(tau0 + 4 * h + 3, 4 * h + 3, mir, wb, cur.x);
+      }
+      // the results over their inputs (a step without a point writes 0)
+      *block(g4) = res;
+      cur = nxt;
     }
-    // the block's results over its inputs; an idle step keeps its slot's value
-    // (a slot without a point holds no value anyone reads)
-    *block(g) = res;
-    cur = nxt;
+    // the producers' ring words at the next block's first step
+    B0 += kPackedBlock * RW;
+    B1 += kPackedBlock * RW;
+    B2 += kPackedBlock * RW;
+    if (B0 >= RG * RW) B0 -= RG * RW;
+    if (B1 >= RG * RW) B1 -= RG * RW;
+    if (B2 >= RG * RW) B2 -= RG * RW;
   }
   cpa_wait<0>();
   __syncthreads();
 }
 
-template <int DX, bool V1>
+template <int DX, bool V1, int Q>
 __global__ void __launch_bounds__(kPackedLanes, 1) packed_kernel(const DevTet *__restrict__ tets,
                                                                  const int *__restrict__ order) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int ti = order ? order[blockIdx.x] : (int)blockIdx.x;
   const DevTet &t = tets[ti];
-  packed_pass<true, DX, V1>(t, smem);
-  packed_pass<false, DX, V1>(t, smem);
+  packed_pass<true, DX, V1, Q>(t, smem);
+  packed_pass<false, DX, V1, Q>(t, smem);
 }
 
-template <int DX>
-cudaError_t launch_dx(const PackedLaunch &L, size_t smem, cudaStream_t st) {
-  auto k = L.v1 ? packed_kernel<DX, true> : packed_kernel<DX, false>;
+template <int DX, bool V1, int Q>
+cudaError_t launch_one(const PackedLaunch &L, size_t smem, cudaStream_t st) {
+  auto k = packed_kernel<DX, V1, Q>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<L.ntets, kPackedLanes, smem, st>>>(L.tets, L.order);
   return cudaGetLastError();
+}
+
+template <int DX>
+cudaError_t launch_dx(const PackedLaunch &L, size_t smem, cudaStream_t st) {
+  switch (L.q * 2 + (L.v1 ? 1 : 0)) {
+    case 2: return launch_one<DX, false, 1>(L, smem, st);
+    case 3: return launch_one<DX, true, 1>(L, smem, st);
+    case 4: return launch_one<DX, false, 2>(L, smem, st);
+    case 5: return launch_one<DX, true, 2>(L, smem, st);
+    case 8: return launch_one<DX, false, 4>(L, smem, st);
+    case 9: return launch_one<DX, true, 4>(L, smem, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Between the lexicographic grid and the packed array, over the residual
@@ -386,7 +443,7 @@ __global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict
 }  // namespace
 
 size_t packed_smem_bytes(int reg) {
-  return (size_t)RG * LN * 4 + (size_t)QS * LN * 16 + (size_t)LN * 32 + (size_t)LN * 4 * (reg + 1) * 8;
+  return (size_t)RR * RW * 4 + (size_t)QS * LN * 16 + (size_t)LN * 32 + (size_t)LN * 4 * (reg + 1) * 8;
 }
 
 cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st) {

@@ -7,17 +7,17 @@
 // other CTA.  Inside the CTA the interior rows (y, z) are packed onto the
 // lanes: a lane owns one row at a time, keeps that row's surrogate
 // polynomials in registers and computes one point of it per step; the CTA
-// advances one step per block barrier.
+// meets at a block barrier every q steps (q, the schedule's quantum: 1, 2 or
+// 4 by level).
 //
 // The schedule -- which lane owns which row from which step on -- is computed
-// on the host once per level: rows in the order of their natural first
-// hyperplane x + 2y + 3z go to the lane that frees up first, with one delay
-// for all later rows whenever no lane is free, so that every producer row
-// keeps a delay no larger than that of its consumers and dependencies keep
-// their order.  The backward substitution runs the same schedule backwards in
-// time (step T - 1 - tau of the forward pass): every forward dependency,
-// reversed, is a backward one, so the reversed schedule is valid, and every
-// row stays on its lane.
+// on the host once per level (packed_plan.cpp): a list schedule that starts
+// each row as soon as its producer rows are far enough ahead and a lane is
+// free, with row starts on multiples of the quantum so that the lanes of a
+// warp change rows on the same few steps.  The backward substitution runs
+// the same schedule backwards in time (step T - 1 - tau of the forward
+// pass): every forward dependency, reversed, is a backward one, so the
+// reversed schedule is valid, and every row stays on its lane.
 //
 // Packed layout.  Point (x, y, z) of a row that starts at forward step s on
 // lane l has the slot (s + x - 1, l) of a float array of T steps x
@@ -35,9 +35,11 @@ namespace ilu {
 
 constexpr int kPackedLanes = 384;  // threads (row lanes) of a packed CTA
 constexpr int kPackedRing = 32;    // steps of each lane's results kept in shared memory
+constexpr int kPackedRingRow = kPackedLanes + 8;  // words per ring row (column kPackedLanes is never written)
 constexpr int kPackedQueue = 8;    // input queue slots per lane
 constexpr int kPackedPre = 7;      // input prefetch distance in steps (below the slot count: the
                                    // entry read at a step is never the one being refilled)
+constexpr int kPackedBlock = 8;    // steps per unrolled block of the kernels' loop; T is a multiple
 constexpr int kPackedMaxLevel = 8; // highest level the packed kernels take
 constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fill the shared memory)
 
@@ -45,18 +47,28 @@ constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fil
 // producer rows are (bits 30-31 the mode): the producer's lane in bits 0-8,
 // the step distance k0 of the first value the consumer reads at a step (the
 // second is written one step later) in bits 9-29, and
-//   kProdNone    no such interior row (the values are masked to 0);
-//   kProdRing    k0 <= kPackedRing - 1: read from the producer lane's ring;
+//   kProdNone    no such interior row (read from the ring column nothing
+//                writes: 0);
+//   kProdRing    k0 <= min(kPackedRing - 1, kPackedRing + 1 - q): read from
+//                the producer lane's ring;
 //   kProdGlobal  further behind: read back from the packed array in global
 //                memory, prefetched like the inputs.
 enum { kProdNone = 0, kProdRing = 1, kProdGlobal = 2 };
 inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 9); }
 
-// One row of a schedule (32 bytes): step of its first point; n | y << 10 |
-// z << 20 (n = points of the row); grid index of its point x = 0; row id;
-// the three producer codes; 1 if a producer is kProdGlobal, else 0.
+// One row of a schedule (32 bytes), in the pass's own steps:
+//   sw_dlo  sw | (lo - sw) << 16: the switch step sw (q - 1 mod q) and the
+//           step lo of the row's first point (lo - sw in 1..q);
+//   nyz     n | y << 10 | z << 20 (n = points of the row);
+//   r01g    R0 | R1 << 14 | far << 28, r2rid R2 | row id << 14: R_j is the
+//           ring word of producer j's value read at the first step of the
+//           kPackedBlock-step block holding sw (kPackedLanes if the producer
+//           row does not exist or comes through the queue), bit j of far set
+//           if producer j comes through the queue;
+//   tt0     the row coordinate t of the point at step sw (float bits);
+//   p[3]    the three producer codes.
 struct PackedEntry {
-  int start, nyz, gb, rid, p[3], far;
+  int sw_dlo, nyz, r01g, r2rid, tt0, p[3];
 };
 
 // slot of step s, lane l in the packed array
@@ -64,21 +76,29 @@ struct PackedEntry {
 __host__ __device__
 #endif
 inline size_t packed_index(int s, int l) { return ((size_t)(s >> 2) * kPackedLanes + l) * 4 + (s & 3); }
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int packed_index32(int s, int l) { return (((s >> 2) * kPackedLanes + l) << 2) + (s & 3); }
 
 struct PackedPlan {
-  int N = 0, lanes = 0, nsteps = 0;  // nsteps = T, the steps of either pass
+  int N = 0, lanes = 0, q = 1, nsteps = 0;  // q: the start quantum; nsteps = T, the steps of either pass
+                                            // (a multiple of kPackedBlock)
   std::vector<PackedEntry> fwd, bwd;  // grouped by lane, each lane's rows in step order
   std::vector<int> lane_off;          // lanes + 1 offsets into either list
   std::vector<int> row_map;           // per row id: forward first step | lane << 20
 };
 
-// Schedule of a level-L tet (N = 2^L) on `lanes` lanes.  The forward
-// producers of row (y, z) are (y-1, z), (y, z-1), (y+1, z-1); the backward
-// ones (y+1, z), (y, z+1), (y-1, z+1).  False (with err) if a check of the
+// Schedule of a level-L tet (N = 2^L) on `lanes` lanes with row starts on
+// multiples of q (1, 2 or 4).  The forward producers of row (y, z) are
+// (y-1, z), (y, z-1), (y+1, z-1); the backward ones (y+1, z), (y, z+1),
+// (y-1, z+1).  False (with err) if a check of the schedule fails.
+bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err);
+// The start quantum of the kernels' schedules at N.
+int packed_quantum(int N);
+// The plan on kPackedLanes lanes with the level's quantum, computed once per
+// level and kept for the life of the process; null (with err) if the
 // schedule fails.
-bool make_packed_plan(int N, int lanes, PackedPlan *out, std::string *err);
-// The plan on kPackedLanes lanes, computed once per level and kept for the
-// life of the process; null (with err) if the schedule fails.
 const PackedPlan *packed_plan_cached(int N, std::string *err);
 
 }  // namespace ilu

@@ -8,33 +8,47 @@
 // lower neighbours of a point lie in rows (y-1, z) (s, se), (y, z-1) (bc, be)
 // and (y+1, z-1) (bnw, bn), whose first hyperplanes are 2, 3 and 1 earlier.
 //
-// Forward schedule.  Rows sorted by natural first hyperplane go, one by one,
-// to the lane that is free first; the row starts at its natural hyperplane
-// plus the current delay, or later if its lane is still busy, and the delay
-// grows to match.  Delays never decrease along the order, so a producer row
-// (always earlier in the order) has at most the delay of its consumer: every
-// value is produced at an earlier step than the step that reads it.
+// Forward schedule (list scheduling).  A row is ready once its producers
+// have starts; it may start q + 1 - c steps after each producer starts (c = 1
+// for (y+1, z-1), whose first hyperplane is one earlier, else 0), which puts
+// every value it reads at least q steps before the step that reads it: the
+// kernels meet at a block barrier only every q steps, after steps q - 1
+// (mod q), so a value is visible to every lane q steps after it was written
+// at the latest.  Ready rows, earliest allowed start first (ties: natural
+// first hyperplane), go to the lane that frees up first, and start when both
+// are ready.  Starts are multiples of the quantum q and rows take
+// ceil(n / q) * q steps (the last ones idle), so that a lane changes rows only
+// on steps q - 1 (mod q) in both passes: the kernels test for that only
+// there.  q is 1 up to level 6 (where the dependency depth sets the step
+// count, and a larger q would lengthen it), 2 at level 7 and 4 at level 8
+// (where the lanes' total work does).
 //
 // Backward schedule.  The same assignment run backwards: forward step tau is
-// backward step T - 1 - tau (T rounded up to whole four-step blocks).  A row
-// of n points on forward steps [s, s+n-1] covers backward steps
-// [T - s - n, T - 1 - s], its point x at backward step T - s - x.  The upper neighbours of a point are the points that read it in
-// the forward pass, so they were computed later there and come earlier here.
+// backward step T - 1 - tau (T rounded up to whole kPackedBlock-step
+// blocks).  A row of n points (n' padded) on forward steps [s, s+n'-1]
+// covers backward steps [T - s - n', T - 1 - s], its point x at backward
+// step T - s - x.  The upper neighbours of a point are the points that read
+// it in the forward pass, so they were computed later there and come earlier
+// here.
 //
-// Spacing on a lane.  Before each row the lane has one idle step (it switches
-// to the row there), and the copy of the following row's coefficients and
-// schedule entry, issued at the end of a row's first step, needs
-// kPackedPre + 1 steps: consecutive rows A, B of a lane keep
-//     s_B >= s_A + n_A + 1,  s_B >= s_A + kPackedPre + 2          (forward)
-//     s_B + n_B >= s_A + n_A + kPackedPre + 2                      (backward,
-// where B comes first and its first backward step is T - s_B - n_B).
+// Spacing on a lane.  Before each row the lane has one step without a point
+// (it switches to the row there), and so has every step after a row's last
+// point.  The copy of a row's coefficients and of the schedule entry after
+// it is issued kPackedPre steps before the row's switch step, when the stage
+// is free: the previous row's switch read it at least a step earlier.  So
+// consecutive rows A, B of a lane (padded lengths n'_A, n'_B) keep
+//     s_B >= s_A + n'_A + 1,  s_B >= s_A + kPackedPre + 2          (forward)
+//     s_B + n'_B >= s_A + n'_A + kPackedPre + 2                    (backward,
+// where B comes first and switches at T - s_B - n'_B - 1).
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <queue>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "grid.h"
@@ -42,64 +56,90 @@
 
 namespace ilu {
 
-bool make_packed_plan(int N, int lanes, PackedPlan *out, std::string *err) {
-  if (N < 4 || N > 256 || lanes < 1 || lanes > 511) {
+int packed_quantum(int N) { return N <= 64 ? 1 : (N <= 128 ? 2 : 4); }
+
+bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err) {
+  if (N < 4 || N > 256 || lanes < 1 || lanes > 511 || (q != 1 && q != 2 && q != 4)) {
     *err = "packed schedule: bad size";
     return false;
   }
-  struct Row {
-    int st, y, z, n;
-  };
-  std::vector<Row> rows;
-  rows.reserve((size_t)num_rows(N));
-  for (int z = 1; z <= N - 3; ++z)
-    for (int y = 1; y <= N - 2 - z; ++y) rows.push_back({1 + 2 * y + 3 * z, y, z, N - 1 - y - z});
-  std::stable_sort(rows.begin(), rows.end(), [](const Row &a, const Row &b) { return a.st < b.st; });
   const int64_t R = num_rows(N);
-  std::vector<int> t_of(R, -1), lane_of(R, -1), yz_of(R, 0);  // first step, lane, y | z << 16 (by row_id)
-  for (const Row &r : rows) yz_of[row_id(N, r.y, r.z)] = r.y | (r.z << 16);
-  using Free = std::pair<int, int>;  // (first step the lane could take, lane)
+  std::vector<int> y_of(R), z_of(R), n_of(R), nat(R), pending(R, 0);
+  std::vector<std::vector<int>> cons(R);
+  auto rid = [&](int y, int z) -> int64_t {
+    return (y >= 1 && z >= 1 && y + z <= N - 2) ? row_id(N, y, z) : -1;
+  };
+  // forward producers of row (y, z) and their c (the first value a consumer
+  // reads at a step is the producer's value c steps after the one at the
+  // consumer's own x)
+  const int pdy[3] = {-1, 0, 1}, pdz[3] = {0, -1, -1}, pc[3] = {0, 0, 1};
+  for (int z = 1; z <= N - 3; ++z)
+    for (int y = 1; y <= N - 2 - z; ++y) {
+      const int64_t id = row_id(N, y, z);
+      y_of[id] = y;
+      z_of[id] = z;
+      n_of[id] = N - 1 - y - z;
+      nat[id] = 1 + 2 * y + 3 * z;
+      for (int j = 0; j < 3; ++j) {
+        const int64_t p = rid(y + pdy[j], z + pdz[j]);
+        if (p >= 0) {
+          ++pending[id];
+          cons[p].push_back((int)id);
+        }
+      }
+    }
+  // list schedule: ready rows by earliest start, then natural hyperplane
+  using Ready = std::tuple<int, int, int>;  // (earliest start, natural first hyperplane, row)
+  std::priority_queue<Ready, std::vector<Ready>, std::greater<Ready>> ready;
+  for (int64_t id = 0; id < R; ++id)
+    if (pending[id] == 0) ready.push({1, nat[id], (int)id});
+  using Free = std::pair<int, int>;  // (first step the lane could take a row at, lane)
   std::priority_queue<Free, std::vector<Free>, std::greater<Free>> freeq;
   for (int l = 0; l < lanes; ++l) freeq.push({1, l});
-  std::vector<int> last_t(lanes, -1), last_n(lanes, 0);  // the lane's previous row
+  std::vector<int> s_of(R, -1), lane_of(R, -1), last_s(lanes, -1), last_np(lanes, 0);
   std::vector<std::vector<int>> per_lane(lanes);
-  int delay = 0, T = 0;
-  for (const Row &r : rows) {
+  auto padded = [&](int n) { return (n + q - 1) / q * q; };
+  int T = 0, done = 0;
+  while (!ready.empty()) {
+    const Ready rd = ready.top();
+    ready.pop();
+    const int id = std::get<2>(rd);
     const Free f = freeq.top();
     freeq.pop();
-    const int l = f.second;
-    int t = std::max(r.st + delay, f.first);
-    if (last_t[l] >= 0) t = std::max(t, last_t[l] + last_n[l] + kPackedPre + 2 - r.n);  // backward spacing
-    delay = t - r.st;
-    const int64_t id = row_id(N, r.y, r.z);
-    t_of[id] = t;
+    const int l = f.second, np = padded(n_of[id]);
+    int s = std::max(std::get<0>(rd), f.first);
+    if (last_s[l] >= 0)
+      s = std::max({s, last_s[l] + last_np[l] + 1, last_s[l] + kPackedPre + 2,
+                    last_s[l] + last_np[l] + kPackedPre + 2 - np});
+    s = (s + q - 1) / q * q;
+    s_of[id] = s;
     lane_of[id] = l;
-    per_lane[l].push_back((int)id);
-    last_t[l] = t;
-    last_n[l] = r.n;
-    freeq.push({t + std::max(r.n + 1, kPackedPre + 2), l});
-    T = std::max(T, t + r.n + 1);  // one idle step after the last point: every backward first step >= 1
+    per_lane[l].push_back(id);
+    last_s[l] = s;
+    last_np[l] = np;
+    freeq.push({s + np + 1, l});
+    T = std::max(T, s + np + 1);  // an idle step after the last row: every backward switch step >= 0
+    ++done;
+    for (int c : cons[id])
+      if (--pending[c] == 0) {
+        int e = 1;
+        for (int j = 0; j < 3; ++j) {
+          const int64_t p = rid(y_of[c] + pdy[j], z_of[c] + pdz[j]);
+          if (p >= 0) e = std::max(e, s_of[p] + q + 1 - pc[j]);
+        }
+        ready.push({e, nat[c], c});
+      }
   }
-  // producer code of (qy, qz) for consumer (y, z): the first value the
-  // consumer reads at a step is written k0 = (first step of the consumer) -
-  // (first step of the producer) + c steps earlier
-  auto code = [&](int y, int z, int qy, int qz, int c, bool fwd, int *out_code) -> bool {
-    if (qy < 1 || qz < 1 || qy + qz > N - 2) {
-      *out_code = prod_code(kProdNone, 0, 0);
-      return true;
-    }
-    const int64_t q = row_id(N, qy, qz), r = row_id(N, y, z);
-    const int nq = N - 1 - qy - qz, nr = N - 1 - y - z;
-    const int sr = fwd ? t_of[r] : T - t_of[r] - nr, sq = fwd ? t_of[q] : T - t_of[q] - nq;
-    const int k0 = sr - sq + c;
-    if (k0 < 2) return false;  // the first value would not be ready
-    if (k0 >= (1 << 21)) return false;
-    *out_code = prod_code(k0 <= kPackedRing - 1 ? kProdRing : kProdGlobal, lane_of[q], k0);
-    return true;
-  };
-  T = (T + 3) & ~3;  // whole four-step blocks of the packed array
+  T = (T + kPackedBlock - 1) / kPackedBlock * kPackedBlock;  // whole blocks of the kernels' loop
+  if (done != R || T >= (1 << 16) || R >= (1 << 18)) {
+    *err = "packed schedule: rows lost or too many steps";
+    return false;
+  }
+  // first point of row r in a pass (backward: the forward schedule reversed in time)
+  auto first = [&](int64_t r, bool fwd) { return fwd ? s_of[r] : T - s_of[r] - n_of[r]; };
   out->N = N;
   out->lanes = lanes;
+  out->q = q;
   out->nsteps = T;
   out->fwd.clear();
   out->bwd.clear();
@@ -107,6 +147,11 @@ bool make_packed_plan(int N, int lanes, PackedPlan *out, std::string *err) {
   out->bwd.reserve((size_t)R);
   out->lane_off.assign((size_t)lanes + 1, 0);
   out->row_map.assign((size_t)R, 0);
+  const double hh = 0.5 / N;
+  // the kernels meet at a block barrier every q steps, so lanes can be up to
+  // q - 1 steps apart: a value read from the ring must not be overwritten by
+  // then (k0 <= kPackedRing + 1 - q)
+  const int ring_max = std::min(kPackedRing - 1, kPackedRing + 1 - q);
   for (int l = 0; l < lanes; ++l) {
     out->lane_off[l] = (int)out->fwd.size();
     const std::vector<int> &ids = per_lane[l];
@@ -114,28 +159,46 @@ bool make_packed_plan(int N, int lanes, PackedPlan *out, std::string *err) {
       for (int pass = 0; pass < 2; ++pass) {
         const bool fwd = pass == 0;
         const int id = fwd ? ids[k] : ids[ids.size() - 1 - k];  // backward: the lane's rows in reverse
-        const int y = yz_of[id] & 0xffff, z = yz_of[id] >> 16, n = N - 1 - y - z;
-        int c[3];
-        const bool ok = fwd ? code(y, z, y - 1, z, 0, true, &c[0]) && code(y, z, y, z - 1, 0, true, &c[1]) &&
-                                  code(y, z, y + 1, z - 1, 1, true, &c[2])
-                            : code(y, z, y + 1, z, 1, false, &c[0]) && code(y, z, y, z + 1, 1, false, &c[1]) &&
-                                  code(y, z, y - 1, z + 1, 1, false, &c[2]);
-        if (!ok) {
-          *err = "packed schedule: a producer value is not ready in time";
-          return false;
+        const int y = y_of[id], z = z_of[id], n = n_of[id], np = padded(n);
+        const int lo = first(id, fwd);
+        const int sw = fwd ? s_of[id] - 1 : T - s_of[id] - np - 1;  // a multiple of q, minus 1
+        const int tau0 = sw & ~(kPackedBlock - 1);
+        int code[3], R3[3], gm = 0;
+        for (int j = 0; j < 3; ++j) {
+          // producers: forward (y-1, z), (y, z-1), (y+1, z-1); backward (y+1, z), (y, z+1), (y-1, z+1)
+          const int64_t p = fwd ? rid(y + pdy[j], z + pdz[j]) : rid(y - pdy[j], z - pdz[j]);
+          if (p < 0) {
+            code[j] = prod_code(kProdNone, 0, 0);
+            R3[j] = kPackedLanes;  // the ring column nothing writes
+            continue;
+          }
+          const int k0 = lo - first(p, fwd) + (fwd ? pc[j] : 1);
+          if (k0 < q + 1 || k0 >= (1 << 21)) {
+            *err = "packed schedule: a producer value is not ready in time";
+            return false;
+          }
+          const bool ring = k0 <= ring_max;
+          code[j] = prod_code(ring ? kProdRing : kProdGlobal, lane_of[p], k0);
+          R3[j] = ring ? ((tau0 + 1 - k0) & (kPackedRing - 1)) * kPackedRingRow + lane_of[p] : kPackedLanes;
+          gm |= ring ? 0 : 1 << j;
         }
-        const int start = fwd ? t_of[id] : T - t_of[id] - n;
-        int far = 0;  // some producer read back from global memory
-        for (int j = 0; j < 3; ++j) far |= ((c[j] >> 30) & 3) == kProdGlobal;
-        (fwd ? out->fwd : out->bwd)
-            .push_back({start, n | (y << 10) | (z << 20), (int)grid_index(N, 0, y, z), id, {c[0], c[1], c[2]}, far});
+        const int K = N - y - z, xsw = fwd ? 0 : n + lo - sw;
+        const float tt0 = (float)((double)(2 * xsw - K) * hh);
+        PackedEntry e;
+        e.sw_dlo = sw | ((lo - sw) << 16);
+        e.nyz = n | (y << 10) | (z << 20);
+        e.r01g = R3[0] | (R3[1] << 14) | (gm << 28);
+        e.r2rid = R3[2] | (id << 14);
+        std::memcpy(&e.tt0, &tt0, sizeof(float));
+        for (int j = 0; j < 3; ++j) e.p[j] = code[j];
+        (fwd ? out->fwd : out->bwd).push_back(e);
       }
-      out->row_map[ids[k]] = t_of[ids[k]] | (l << 20);
+      out->row_map[ids[k]] = s_of[ids[k]] | (l << 20);
     }
   }
   out->lane_off[lanes] = (int)out->fwd.size();
-  if ((int64_t)out->fwd.size() != R || T >= (1 << 20)) {
-    *err = "packed schedule: rows lost or too many steps";
+  if ((int64_t)out->fwd.size() != R) {
+    *err = "packed schedule: rows lost";
     return false;
   }
   return true;
@@ -148,7 +211,7 @@ const PackedPlan *packed_plan_cached(int N, std::string *err) {
   auto &slot = cache[N];
   if (!slot) {
     auto p = std::make_unique<PackedPlan>();
-    if (!make_packed_plan(N, kPackedLanes, p.get(), err)) return nullptr;
+    if (!make_packed_plan(N, kPackedLanes, packed_quantum(N), p.get(), err)) return nullptr;
     slot = std::move(p);
   }
   return slot.get();

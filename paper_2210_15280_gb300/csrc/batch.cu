@@ -94,12 +94,13 @@ struct ilu_batch_s {
   std::vector<Group> groups;
   std::vector<PackedGroup> pgroups;
   int *d_porder = nullptr;  // tet order of the packed launches
-  int *d_rlists = nullptr;  // per operator kind: tet order, then block prefix (residual launches)
-  int rn[3] = {0, 0, 0}, rblocks[3] = {0, 0, 0};
+  int2 *d_rmap = nullptr;  // per operator kind: (tet, its block) of each block of its residual launch
+  int rblocks[3] = {0, 0, 0};
   size_t rat[3] = {0, 0, 0};
   int total_blocks = 0, nflags = 0;
   DevTet *d_tets = nullptr;
-  int *d_bprefix = nullptr, *d_maps = nullptr, *d_flags = nullptr;
+  int2 *d_iomap = nullptr;  // (tet, its block) of each block of the update launch
+  int *d_maps = nullptr, *d_flags = nullptr;
   void **d_ptrs = nullptr;  // xs[n] then bs[n]
   void **h_ptrs = nullptr;  // pinned staging of the pointer arrays
   cudaEvent_t ptr_ev = nullptr, fork = nullptr;
@@ -133,21 +134,22 @@ void free_plan(ilu_batch b) {
   b->pgroups.clear();
   cudaFree(b->d_porder);
   b->d_porder = nullptr;
-  cudaFree(b->d_rlists);
-  b->d_rlists = nullptr;
+  cudaFree(b->d_rmap);
+  b->d_rmap = nullptr;
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->ptr_ev) cudaEventDestroy(b->ptr_ev);
   if (b->fork) cudaEventDestroy(b->fork);
   b->cap = nullptr;
   b->ptr_ev = b->fork = nullptr;
   cudaFree(b->d_tets);
-  cudaFree(b->d_bprefix);
+  cudaFree(b->d_iomap);
   cudaFree(b->d_maps);
   cudaFree(b->d_flags);
   cudaFree(b->d_ptrs);
   cudaFree(b->d_status);
   b->d_tets = nullptr;
-  b->d_bprefix = b->d_maps = b->d_flags = nullptr;
+  b->d_iomap = nullptr;
+  b->d_maps = b->d_flags = nullptr;
   b->d_ptrs = nullptr;
   b->d_status = nullptr;
   if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
@@ -238,34 +240,32 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   }
   const int ticket0 = off;
   b->nflags = off + 2 * (int)b->groups.size();
-  // residual block ranges
-  std::vector<int> bprefix(n + 1, 0);
-  for (int i = 0; i < n; ++i) bprefix[i + 1] = bprefix[i] + residual_blocks(b->views[i].N);
-  b->total_blocks = bprefix[n];
+  // block maps of the residual and update launches: (tet, its block)
+  std::vector<int2> iomap;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < residual_blocks(b->views[i].N); ++k) iomap.push_back(make_int2(i, k));
+  b->total_blocks = (int)iomap.size();
   BK(cudaMalloc(&b->d_flags, sizeof(int) * b->nflags), "cudaMalloc flags");
   BK(cudaMemset(b->d_flags, 0, sizeof(int) * b->nflags), "cudaMemset flags");
   for (auto &d : b->dev) d.flags = b->d_flags;
   BK(cudaMalloc(&b->d_tets, sizeof(DevTet) * n), "cudaMalloc tets");
   BK(cudaMemcpy(b->d_tets, b->dev.data(), sizeof(DevTet) * n, cudaMemcpyHostToDevice), "upload tets");
-  BK(cudaMalloc(&b->d_bprefix, sizeof(int) * (n + 1)), "cudaMalloc block prefix");
-  BK(cudaMemcpy(b->d_bprefix, bprefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice), "upload prefix");
-  {  // residual launches by operator kind: per kind the tets and their block prefix
-    std::vector<int> lists;
+  BK(cudaMalloc(&b->d_iomap, sizeof(int2) * std::max<size_t>(iomap.size(), 1)), "cudaMalloc block map");
+  if (!iomap.empty())
+    BK(cudaMemcpy(b->d_iomap, iomap.data(), sizeof(int2) * iomap.size(), cudaMemcpyHostToDevice), "upload block map");
+  {  // residual launches by operator kind: the blocks of that kind's tets
+    std::vector<int2> rmap;
     for (int op = 0; op < 3; ++op) {
-      std::vector<int> ids;
+      b->rat[op] = rmap.size();
       for (int i = 0; i < n; ++i)
-        if (residual_op(b->dev[i]) == op) ids.push_back(i);
-      b->rn[op] = (int)ids.size();
-      b->rat[op] = lists.size();
-      lists.insert(lists.end(), ids.begin(), ids.end());
-      int acc = 0;
-      lists.push_back(0);
-      for (int i : ids) lists.push_back(acc += residual_blocks(b->views[i].N));
-      b->rblocks[op] = acc;
+        if (residual_op(b->dev[i]) == op)
+          for (int k = 0; k < residual_blocks(b->views[i].N); ++k) rmap.push_back(make_int2(i, k));
+      b->rblocks[op] = (int)(rmap.size() - b->rat[op]);
     }
-    BK(cudaMalloc(&b->d_rlists, sizeof(int) * lists.size()), "cudaMalloc residual lists");
-    BK(cudaMemcpy(b->d_rlists, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice),
-       "upload residual lists");
+    BK(cudaMalloc(&b->d_rmap, sizeof(int2) * std::max<size_t>(rmap.size(), 1)), "cudaMalloc residual maps");
+    if (!rmap.empty())
+      BK(cudaMemcpy(b->d_rmap, rmap.data(), sizeof(int2) * rmap.size(), cudaMemcpyHostToDevice),
+         "upload residual maps");
   }
   BK(cudaMalloc(&b->d_ptrs, sizeof(void *) * 2 * n), "cudaMalloc pointer arrays");
   BK(cudaMemset(b->d_ptrs, 0, sizeof(void *) * 2 * n), "cudaMemset pointer arrays");
@@ -369,8 +369,7 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
   for (int k = 0; k < sweeps; ++k) {
     BK(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * b->nflags, s), "reset flags");
     for (int op = 0; op < 3; ++op) {
-      const int *order = b->d_rlists + b->rat[op];
-      BK(launch_residual_batch(b->d_tets, order, order + b->rn[op], b->rn[op], b->rblocks[op], b->kind, op,
+      BK(launch_residual_batch(b->d_tets, b->d_rmap + b->rat[op], b->rblocks[op], b->kind, op,
                                b->d_ptrs, b->d_ptrs + b->n, s),
          "batched residual launch");
     }
@@ -389,7 +388,7 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
       BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
     }
     if (!b->pgroups.empty())  // x += the packed tets' results (the slab tets updated x themselves)
-      BK(launch_packed_io(0, b->kind == kSweepMixed, b->d_tets, b->d_bprefix, b->n, b->total_blocks, b->d_ptrs,
+      BK(launch_packed_io(0, b->kind == kSweepMixed, b->d_tets, b->d_iomap, b->total_blocks, b->d_ptrs,
                           nullptr, s),
          "packed update launch");
   }

@@ -649,7 +649,7 @@ ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStre
       CK(launch_packed(t->pl, st), "packed substitution launch");
     }
     Traced tr(t, 2, st);  // x += w (traced as the backward)
-    CK(launch_packed_io(0, t->precision != ILU_F32, t->d_dev, nullptr, 1, used, nullptr, x, st), "update launch");
+    CK(launch_packed_io(0, t->precision != ILU_F32, t->d_dev, nullptr, used, nullptr, x, st), "update launch");
     return ILU_OK;
   }
   {
@@ -692,14 +692,14 @@ ilu_status precond(ilu_tet t, const void *r, void *z, cudaStream_t st) {
   if (t->use_packed) {  // r into the packed array, the substitutions, z = their result
     const int nb = residual_blocks(t->host.N);
     t->launches++;
-    CK(launch_packed_io(1, vf64, t->d_dev, nullptr, 1, nb, nullptr, const_cast<void *>(r), st), "copy launch");
+    CK(launch_packed_io(1, vf64, t->d_dev, nullptr, nb, nullptr, const_cast<void *>(r), st), "copy launch");
     CK(cudaMemsetAsync(z, 0, n * t->elem(), st), "clear z");
     {
       Traced tr(t, 1, st);
       CK(launch_packed(t->pl, st), "packed substitution launch");
     }
     Traced tr(t, 2, st);
-    CK(launch_packed_io(0, vf64, t->d_dev, nullptr, 1, nb, nullptr, z, st), "update launch");
+    CK(launch_packed_io(0, vf64, t->d_dev, nullptr, nb, nullptr, z, st), "update launch");
     return ILU_OK;
   }
   CK(launch_copy(vf64, wf64, r, t->d_w, n, st), "copy launch");

@@ -78,6 +78,62 @@ ILU_HD int64_t row_id(int N, int y, int z) {
 // interior x-range of row (y,z) is [1, N-1-y-z]; its centre
 ILU_HD int row_len(int N, int y, int z) { return N - 1 - y - z; }
 
+// ---- 32-bit forms for the kernels (every grid index fits for N <= 1024,
+// level 10).  Grid index of (0, y, z); row id.
+ILU_HD int row_start32(int N, int y, int z) {
+  const int a = N + 1, b = N + 1 - z;
+  return (a * (a + 1) * (a + 2) - b * (b + 1) * (b + 2)) / 6 + y * (N - z + 1) - y * (y - 1) / 2;
+}
+ILU_HD int row_id32(int N, int y, int z) { return (z - 1) * (N - 2) - (z - 1) * z / 2 + (y - 1); }
+// The grid indices of (0, .) of the seven rows a stencil at (x, y, z) touches,
+// from r0 = row_start32(N, y, z): layer z' holds (N - z' + 1)(N - z' + 2) / 2
+// points, row (y, z) N - z - y + 1.
+struct StencilRows {
+  int r0, rs, rn, rb, rbn, rt, rts;  // (y,z) (y-1,z) (y+1,z) (y,z-1) (y+1,z-1) (y,z+1) (y-1,z+1)
+};
+ILU_HD StencilRows stencil_rows(int N, int y, int z) {
+  StencilRows R;
+  const int m = N - z - y;  // row (y, z) has m + 1 points
+  R.r0 = row_start32(N, y, z);
+  R.rs = R.r0 - (m + 2);
+  R.rn = R.r0 + (m + 1);
+  R.rb = R.r0 - (N - z + 2) * (N - z + 3) / 2 + y;
+  R.rbn = R.rb + m + 2;
+  R.rt = R.r0 + (N - z + 1) * (N - z + 2) / 2 - y;
+  R.rts = R.rt - (m + 1);
+  return R;
+}
+
+// ---- residual chunks: the interior points in lexicographic order (x fastest,
+// then y, then z), cut into runs of 32; a chunk is the first point of its run,
+// x | y << 10 | z << 20.  Lane `lane` of a warp takes the run's point number
+// `lane`: false past the last interior point.  All 32 lanes must call it
+// together: the rows are stepped through in a warp-uniform loop, so the warp
+// leaves it converged (a loop that each lane left on its own would leave the
+// lanes to run the stencil arithmetic that follows in separate groups).
+#if defined(__CUDACC__)
+__device__ __forceinline__ bool chunk_point(int N, int ch, int lane, int &x, int &y, int &z) {
+  x = (ch & 1023) + lane;
+  y = (ch >> 10) & 1023;
+  z = ch >> 20;
+  bool ok = true;
+  int n = N - 1 - y - z;
+  bool more = x > n;
+  while (__any_sync(0xffffffffu, more)) {  // the run continues in the next rows (a few at most)
+    if (more) {
+      x -= n;
+      if (++y > N - 2 - z) {
+        y = 1;
+        if (++z > N - 3) ok = false;
+      }
+      n = N - 1 - y - z;
+      more = ok && x > n;
+    }
+  }
+  return ok;
+}
+#endif
+
 // ---- boundary variant V1: the interior points on the cell boundary (a
 // neighbour in D outside the interior) keep their exact factors.  Rows with
 // y = 1 or z = 1 lie wholly on it; every other row has its first (x = 1) and

@@ -27,10 +27,10 @@ namespace {
 
 // --------------------------------------------------------------- residual --
 
-// Where a row's operator comes from: the constant stencil, or the edge-star
-// weights and kappa at the grid points, or the stored coefficients.
+// Where a point's operator comes from: the constant stencil (passed in
+// registers), or the edge-star weights and kappa at the grid points, or the
+// stored coefficients.
 struct StencilData {
-  const void *A15;     // the constant stencil in the residual type (a per-block copy)
   const double *Wstar, *kappa;
   const void *astore;  // stored off-diagonal coefficients (MODE 2)
   int64_t astride;
@@ -39,105 +39,116 @@ struct StencilData {
 // MODE of the operator (kernels.cuh): constant stencil, assembled on the fly
 // from kappa, or stored coefficients (the same values as on the fly)
 
-// r = b - A x at the interior points x0 + lane of row (y, z) (one warp, one
-// 32-point chunk of the row); returns this lane's share of ||r||^2
+// r = b - A x at the interior point of lane `lane` of chunk `ch` (one warp,
+// 32 consecutive interior points); returns this lane's share of ||r||^2
 // (pmap non-null: r goes to the packed array pw instead, at the slot of the
-// point's row, pmap[row id] = forward first step | lane << 20)
+// point's row, pmap[row id] = forward first step | lane << 20).  A15: the
+// constant stencil (registers for FP32, shared memory for FP64).
 template <typename TX, typename TR, typename TW, int MODE>
-__device__ __forceinline__ double residual_chunk(const StencilData &t, int N, int y, int z, int x0, int lane,
+__device__ __forceinline__ double residual_chunk(const StencilData &t, const TR *A15, int N, int ch, int lane,
                                                  const TX *__restrict__ x, const TX *__restrict__ b,
                                                  TW *__restrict__ r, const int *__restrict__ pmap = nullptr,
                                                  float *__restrict__ pw = nullptr) {
-  double acc2 = 0.0;
-  if (y + z > N - 2) return acc2;
-  const int n = N - 1 - y - z;
-  // row starts of the seven rows the stencil touches
-  const int64_t r0 = grid_index(N, 0, y, z);          // (y, z)
-  const int64_t rs = grid_index(N, 0, y - 1, z);      // (y-1, z)
-  const int64_t rn = grid_index(N, 0, y + 1, z);      // (y+1, z)
-  const int64_t rb = grid_index(N, 0, y, z - 1);      // (y, z-1)
-  const int64_t rbn = grid_index(N, 0, y + 1, z - 1); // (y+1, z-1)
-  const int64_t rt = grid_index(N, 0, y, z + 1);      // (y, z+1)
-  const int64_t rts = grid_index(N, 0, y - 1, z + 1); // (y-1, z+1)
-  {
-    const int xx = x0 + lane;
-    if (xx > n) return acc2;
-    // neighbour values in the order of D: w s se bnw bn bc be c e n nw tse ts tc tw
-    TR xv[15];
-    xv[0] = (TR)x[r0 + xx - 1];
-    xv[1] = (TR)x[rs + xx];
-    xv[2] = (TR)x[rs + xx + 1];
-    xv[3] = (TR)x[rbn + xx - 1];
-    xv[4] = (TR)x[rbn + xx];
-    xv[5] = (TR)x[rb + xx];
-    xv[6] = (TR)x[rb + xx + 1];
-    xv[7] = (TR)x[r0 + xx];
-    xv[8] = (TR)x[r0 + xx + 1];
-    xv[9] = (TR)x[rn + xx];
-    xv[10] = (TR)x[rn + xx - 1];
-    xv[11] = (TR)x[rts + xx + 1];
-    xv[12] = (TR)x[rts + xx];
-    xv[13] = (TR)x[rt + xx];
-    xv[14] = (TR)x[rt + xx - 1];
-    TR res = (TR)b[r0 + xx];
-    if (MODE == kOpConst) {
-      const TR *A15 = static_cast<const TR *>(t.A15);
+  int xx, y, z;
+  if (!chunk_point(N, ch, lane, xx, y, z)) return 0.0;
+  const StencilRows R = stencil_rows(N, y, z);
+  // neighbour values in the order of D: w s se bnw bn bc be c e n nw tse ts tc tw
+  TR xv[15];
+  xv[0] = (TR)x[R.r0 + xx - 1];
+  xv[1] = (TR)x[R.rs + xx];
+  xv[2] = (TR)x[R.rs + xx + 1];
+  xv[3] = (TR)x[R.rbn + xx - 1];
+  xv[4] = (TR)x[R.rbn + xx];
+  xv[5] = (TR)x[R.rb + xx];
+  xv[6] = (TR)x[R.rb + xx + 1];
+  xv[7] = (TR)x[R.r0 + xx];
+  xv[8] = (TR)x[R.r0 + xx + 1];
+  xv[9] = (TR)x[R.rn + xx];
+  xv[10] = (TR)x[R.rn + xx - 1];
+  xv[11] = (TR)x[R.rts + xx + 1];
+  xv[12] = (TR)x[R.rts + xx];
+  xv[13] = (TR)x[R.rt + xx];
+  xv[14] = (TR)x[R.rt + xx - 1];
+  TR res = (TR)b[R.r0 + xx];
+  if (MODE == kOpConst) {
 #pragma unroll
-      for (int d = 0; d < 15; ++d) res = fma(-A15[d], xv[d], res);
-    } else if (MODE == kOpStored) {
-      stored_apply(res, t.astore, t.astride, r0 + xx, xv);
-    } else {
-      const double *kap = t.kappa;
-      double kq[15];
-      kq[0] = kap[r0 + xx - 1];
-      kq[1] = kap[rs + xx];
-      kq[2] = kap[rs + xx + 1];
-      kq[3] = kap[rbn + xx - 1];
-      kq[4] = kap[rbn + xx];
-      kq[5] = kap[rb + xx];
-      kq[6] = kap[rb + xx + 1];
-      kq[7] = kap[r0 + xx];
-      kq[8] = kap[r0 + xx + 1];
-      kq[9] = kap[rn + xx];
-      kq[10] = kap[rn + xx - 1];
-      kq[11] = kap[rts + xx + 1];
-      kq[12] = kap[rts + xx];
-      kq[13] = kap[rt + xx];
-      kq[14] = kap[rt + xx - 1];
-      star_apply_all(std::make_integer_sequence<int, 15>{}, res, kq, xv, t.Wstar);
-    }
-    if (pmap) {
-      const int m = pmap[row_id(N, y, z)];
-      pw[packed_index((m & 0xfffff) + xx - 1, m >> 20)] = (float)res;
-    } else {
-      r[r0 + xx] = (TW)res;
-    }
-    acc2 += (double)res * (double)res;
+    for (int d = 0; d < 15; ++d) res = fma(-A15[d], xv[d], res);
+  } else if (MODE == kOpStored) {
+    stored_apply(res, t.astore, t.astride, (int64_t)R.r0 + xx, xv);
+  } else {
+    const double *kap = t.kappa;
+    double kq[15];
+    kq[0] = kap[R.r0 + xx - 1];
+    kq[1] = kap[R.rs + xx];
+    kq[2] = kap[R.rs + xx + 1];
+    kq[3] = kap[R.rbn + xx - 1];
+    kq[4] = kap[R.rbn + xx];
+    kq[5] = kap[R.rb + xx];
+    kq[6] = kap[R.rb + xx + 1];
+    kq[7] = kap[R.r0 + xx];
+    kq[8] = kap[R.r0 + xx + 1];
+    kq[9] = kap[R.rn + xx];
+    kq[10] = kap[R.rn + xx - 1];
+    kq[11] = kap[R.rts + xx + 1];
+    kq[12] = kap[R.rts + xx];
+    kq[13] = kap[R.rt + xx];
+    kq[14] = kap[R.rt + xx - 1];
+    // the weights are read anew for every point (cached, the same address in
+    // every lane): holding all 100 across the chunk loop would take 200 registers
+    const double *W = t.Wstar;
+    asm volatile("" : "+l"(W));
+    star_apply_all(std::make_integer_sequence<int, 15>{}, res, kq, xv, W);
   }
-  return acc2;
+  if (pmap) {
+    const int m = pmap[row_id32(N, y, z)];
+    pw[packed_index32((m & 0xfffff) + xx - 1, m >> 20)] = (float)res;
+  } else {
+    r[R.r0 + xx] = (TW)res;
+  }
+  return (double)res * (double)res;
 }
 
-// One tet: a warp per kResidualCPW consecutive 32-point chunks of interior
-// rows (the chunk list balances rows of every length), 8 warps per block,
-// per-block partial norms.
+// CTAs per SM the residual launches are compiled for (their register budget)
+template <int MODE>
+constexpr int residual_min_blocks() {
+  return MODE == kOpStar ? 2 : 4;
+}
+
+// The constant stencil of a block in the residual type: FP32 coefficients
+// stay in registers, FP64 ones (30 registers) are read from shared memory.
+template <typename TR, int MODE>
+struct ConstStencil {
+  TR reg[15];
+  __device__ __forceinline__ const TR *load(const double *A, TR *sh) {
+    if (MODE != kOpConst) return reg;
+    if (sizeof(TR) == 4) {
+#pragma unroll
+      for (int d = 0; d < 15; ++d) reg[d] = (TR)A[d];
+      return reg;
+    }
+    if (threadIdx.x < 15) sh[threadIdx.x] = (TR)A[threadIdx.x];
+    __syncthreads();
+    return sh;
+  }
+};
+
+// One tet: a warp per kResidualCPW consecutive 32-point chunks, 8 warps per
+// block, per-block partial norms.
 template <typename TX, typename TR, typename TW, int MODE>
-__global__ void __launch_bounds__(256, MODE == kOpStar ? 1 : 4) residual_kernel(DevTet t, const TX *__restrict__ x,
-                                                       const TX *__restrict__ b, TW *__restrict__ r,
-                                                       double *__restrict__ partials, bool packed) {
+__global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_kernel(
+    DevTet t, const TX *__restrict__ x, const TX *__restrict__ b, TW *__restrict__ r, double *__restrict__ partials,
+    bool packed) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the constant stencil, converted once per block to the residual type
   __shared__ TR sA15[15];
-  if (threadIdx.x < 15) sA15[threadIdx.x] = (TR)t.A15[threadIdx.x];
-  __syncthreads();
-  const StencilData sd{sA15, t.Wstar, t.kappa, t.astore, t.astride};
+  ConstStencil<TR, MODE> cs;
+  const TR *A15 = cs.load(t.A15, sA15);
+  const StencilData sd{t.Wstar, t.kappa, t.astore, t.astride};
   double acc2 = 0.0;
   const int c0 = (blockIdx.x * 8 + warp) * kResidualCPW;  // this warp's consecutive chunks
 #pragma unroll 1
-  for (int k = 0; k < kResidualCPW && c0 + k < t.nchunks; ++k) {
-    const int ch = t.chunks[c0 + k];
-    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, t.N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, x, b,
-                                             r, packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
-  }
+  for (int k = 0; k < kResidualCPW && c0 + k < t.nchunks; ++k)
+    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, A15, t.N, t.chunks[c0 + k], lane, x, b, r,
+                                             packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
   // deterministic block reduction of the squared norm
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
@@ -151,46 +162,33 @@ __global__ void __launch_bounds__(256, MODE == kOpStar ? 1 : 4) residual_kernel(
   }
 }
 
-// Many tets whose operators come the same way (MODE): 1-D grid, tet
-// order[i] owns blocks [bprefix[i], bprefix[i+1]) laid out as its single-tet
-// grid; the result goes to the tet's packed array if it has one, else to its
-// scratch w.  One launch per operator kind keeps the register count of each
-// kernel that of its own arithmetic.
+// Many tets whose operators come the same way (MODE): block i belongs to tet
+// bmap[i].x and is its block bmap[i].y (laid out as the tet's single-tet
+// grid); the result goes to the tet's packed array if it has one, else to
+// its scratch w.  One launch per operator kind keeps the register count of
+// each kernel that of its own arithmetic.
 template <typename TX, typename TR, typename TW, int MODE>
-__global__ void __launch_bounds__(256, MODE == kOpStar ? 1 : 4)
-    residual_batch_kernel(const DevTet *__restrict__ tets, const int *__restrict__ order,
-                          const int *__restrict__ bprefix, int n, const TX *const *__restrict__ xs,
-                          const TX *const *__restrict__ bs) {
-  int lo = 0, hi = n - 1;
-  const int blk = blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (bprefix[mid] <= blk) lo = mid;
-    else hi = mid - 1;
-  }
-  const int ti = order[lo];
-  const DevTet &tg = tets[ti];
-  // the block's stencil weights in shared memory (reading them from the
-  // device array would keep all 100 live in registers)
-  __shared__ double sW[kStarPairs];
-  __shared__ TR sA[15];
-  if (MODE == kOpStar)
-    for (int i = threadIdx.x; i < kStarPairs; i += blockDim.x) sW[i] = tg.Wstar[i];
-  if (threadIdx.x < 15) sA[threadIdx.x] = (TR)tg.A15[threadIdx.x];
-  __syncthreads();
+__global__ void __launch_bounds__(256, residual_min_blocks<MODE>())
+    residual_batch_kernel(const DevTet *__restrict__ tets, const int2 *__restrict__ bmap,
+                          const TX *const *__restrict__ xs, const TX *const *__restrict__ bs) {
+  const int2 bm = bmap[blockIdx.x];
+  const DevTet &tg = tets[bm.x];
+  __shared__ TR sA15[15];
+  ConstStencil<TR, MODE> cs;
+  const TR *A15 = cs.load(tg.A15, sA15);
   const int N = tg.N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = ((blk - bprefix[lo]) * 8 + warp) * kResidualCPW;
+  const int c0 = (bm.y * 8 + warp) * kResidualCPW;
+  const int nch = tg.nchunks;
+  const int *chunks = tg.chunks;
   TW *r = reinterpret_cast<TW *>(tg.w);
-  const StencilData sd{sA, sW, tg.kappa, tg.astore, tg.astride};
+  const StencilData sd{tg.Wstar, tg.kappa, tg.astore, tg.astride};
   const int *pmap = tg.pk.pw ? tg.pk.row_map : nullptr;
-  const TX *xv = xs[ti], *bv = bs[ti];
+  float *pw = tg.pk.pw;
+  const TX *xv = xs[bm.x], *bv = bs[bm.x];
 #pragma unroll 1
-  for (int k = 0; k < kResidualCPW && c0 + k < tg.nchunks; ++k) {  // no block-wide synchronisation follows
-    const int ch = tg.chunks[c0 + k];
-    residual_chunk<TX, TR, TW, MODE>(sd, N, (ch >> 10) & 1023, ch >> 20, 1 + 32 * (ch & 1023), lane, xv, bv, r, pmap,
-                                     tg.pk.pw);
-  }
+  for (int k = 0; k < kResidualCPW && c0 + k < nch; ++k)  // no block-wide synchronisation follows
+    residual_chunk<TX, TR, TW, MODE>(sd, A15, N, chunks[c0 + k], lane, xv, bv, r, pmap, pw);
 }
 
 // ------------------------------------------------- solver vector helpers --
@@ -290,19 +288,15 @@ __global__ void norm_finish_kernel(const double *__restrict__ partials, int n, d
 // ------------------------------------------------------------ launchers --
 
 // 32-point chunks of the interior rows, z-major then y then chunk
-int residual_chunks(int N) {
-  int n = 0;
-  for (int z = 1; z <= N - 3; ++z)
-    for (int y = 1; y <= N - 2 - z; ++y) n += (N - 1 - y - z + 31) / 32;
-  return n;
-}
+int residual_chunks(int N) { return (int)((grid_interior(N) + 31) / 32); }
 int residual_blocks(int N) { return (residual_chunks(N) + 8 * kResidualCPW - 1) / (8 * kResidualCPW); }
 int rowgrid_blocks(int N) { return ((N - 3 + 7) / 8) * (N - 3); }
 void residual_chunk_list(int N, int *out) {
-  int i = 0;
+  int i = 0, k = 0;
   for (int z = 1; z <= N - 3; ++z)
     for (int y = 1; y <= N - 2 - z; ++y)
-      for (int c = 0; c < (N - 1 - y - z + 31) / 32; ++c) out[i++] = z << 20 | y << 10 | c;
+      for (int x = 1; x <= N - 1 - y - z; ++x, ++k)
+        if (k % 32 == 0) out[i++] = x | y << 10 | z << 20;
 }
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
@@ -332,15 +326,15 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual_batch(const DevTet *tets, const int *order, const int *bprefix, int n, int total_blocks,
-                                  int kind, int op, const void *const *xs, const void *const *bs, cudaStream_t st) {
-  if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+cudaError_t launch_residual_batch(const DevTet *tets, const int2 *bmap, int total_blocks, int kind, int op,
+                                  const void *const *xs, const void *const *bs, cudaStream_t st) {
+  if (total_blocks <= 0) return cudaSuccess;
   auto go = [&](auto tx, auto tr, auto tw, auto m) {
     using TX = decltype(tx);
     using TR = decltype(tr);
     using TW = decltype(tw);
     residual_batch_kernel<TX, TR, TW, decltype(m)::value><<<total_blocks, 256, 0, st>>>(
-        tets, order, bprefix, n, reinterpret_cast<const TX *const *>(xs), reinterpret_cast<const TX *const *>(bs));
+        tets, bmap, reinterpret_cast<const TX *const *>(xs), reinterpret_cast<const TX *const *>(bs));
   };
   auto by_op = [&](auto tx, auto tr, auto tw) {
     if (op == kOpConst) go(tx, tr, tw, std::integral_constant<int, kOpConst>{});
@@ -354,36 +348,34 @@ cudaError_t launch_residual_batch(const DevTet *tets, const int *order, const in
 }
 
 namespace {
-// one warp per 32-point row chunk, as the residual
+// one warp per 32-point chunk, as the residual
 template <typename TA>
 __global__ void __launch_bounds__(256) stencil_store_kernel(DevTet t, TA *__restrict__ A) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ci = blockIdx.x * 8 + warp;
   if (ci >= t.nchunks) return;
-  const int ch = t.chunks[ci];
-  const int N = t.N, y = (ch >> 10) & 1023, z = ch >> 20, xx = 1 + 32 * (ch & 1023) + lane;
-  if (y + z > N - 2 || xx > N - 1 - y - z) return;
-  const int64_t r0 = grid_index(N, 0, y, z), rs = grid_index(N, 0, y - 1, z), rn = grid_index(N, 0, y + 1, z);
-  const int64_t rb = grid_index(N, 0, y, z - 1), rbn = grid_index(N, 0, y + 1, z - 1);
-  const int64_t rt = grid_index(N, 0, y, z + 1), rts = grid_index(N, 0, y - 1, z + 1);
+  const int N = t.N;
+  int xx, y, z;
+  if (!chunk_point(N, t.chunks[ci], lane, xx, y, z)) return;
+  const StencilRows R = stencil_rows(N, y, z);
   const double *kap = t.kappa;
   double kq[15];
-  kq[0] = kap[r0 + xx - 1];
-  kq[1] = kap[rs + xx];
-  kq[2] = kap[rs + xx + 1];
-  kq[3] = kap[rbn + xx - 1];
-  kq[4] = kap[rbn + xx];
-  kq[5] = kap[rb + xx];
-  kq[6] = kap[rb + xx + 1];
-  kq[7] = kap[r0 + xx];
-  kq[8] = kap[r0 + xx + 1];
-  kq[9] = kap[rn + xx];
-  kq[10] = kap[rn + xx - 1];
-  kq[11] = kap[rts + xx + 1];
-  kq[12] = kap[rts + xx];
-  kq[13] = kap[rt + xx];
-  kq[14] = kap[rt + xx - 1];
-  star_store_all(std::make_integer_sequence<int, 15>{}, kq, t.Wstar, A, t.astride, r0 + xx);
+  kq[0] = kap[R.r0 + xx - 1];
+  kq[1] = kap[R.rs + xx];
+  kq[2] = kap[R.rs + xx + 1];
+  kq[3] = kap[R.rbn + xx - 1];
+  kq[4] = kap[R.rbn + xx];
+  kq[5] = kap[R.rb + xx];
+  kq[6] = kap[R.rb + xx + 1];
+  kq[7] = kap[R.r0 + xx];
+  kq[8] = kap[R.r0 + xx + 1];
+  kq[9] = kap[R.rn + xx];
+  kq[10] = kap[R.rn + xx - 1];
+  kq[11] = kap[R.rts + xx + 1];
+  kq[12] = kap[R.rts + xx];
+  kq[13] = kap[R.rt + xx];
+  kq[14] = kap[R.rt + xx - 1];
+  star_store_all(std::make_integer_sequence<int, 15>{}, kq, t.Wstar, A, t.astride, (int64_t)R.r0 + xx);
 }
 }  // namespace
 

@@ -68,7 +68,8 @@ struct DevTet {
   PackedDev pk;      // packed substitution schedules (null when not used)
   const void *pkF;   // packed kernels' FP32 row polynomials: [row][k = 0..dx][4 function pairs] float2,
   const void *pkB;   // forward and backward (null when not used)
-  const int *chunks; // residual work list: z << 20 | y << 10 | chunk (32 points of a row)
+  const int *chunks; // residual work list: first point x | y << 10 | z << 20 of each run of 32
+                     // interior points in lexicographic order (chunk_point in grid.h)
   int nchunks;
   const void *astore;    // variable kappa, stored operator: coefficient of direction d (d != centre) of
                          // row p at astore[(d < 7 ? d : d - 1) * astride + p], double (float in F32
@@ -100,13 +101,12 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
 // the fly from kappa at the grid points, or the stored coefficients.
 constexpr int kOpConst = 0, kOpStar = 1, kOpStored = 2;
 inline int residual_op(const DevTet &t) { return t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar); }
-// Residual of many tets with the same residual_op in one launch: tet
-// order[i] owns blocks [bprefix[i], bprefix[i+1]) of the 1-D grid (bprefix[n]
-// = total, residual_blocks(N) each); tets, order, bprefix and the per-tet
-// pointer arrays (indexed by tet) are device memory.  Writes w of each tet,
-// or its packed array if it has one; no norms.
-cudaError_t launch_residual_batch(const DevTet *tets, const int *order, const int *bprefix, int n, int total_blocks,
-                                  int kind, int op, const void *const *xs, const void *const *bs, cudaStream_t st);
+// Residual of many tets with the same residual_op in one launch: block i of
+// the 1-D grid is block bmap[i].y of tet bmap[i].x (residual_blocks(N) per
+// tet); tets, bmap and the per-tet pointer arrays (indexed by tet) are device
+// memory.  Writes w of each tet, or its packed array if it has one; no norms.
+cudaError_t launch_residual_batch(const DevTet *tets, const int2 *bmap, int total_blocks, int kind, int op,
+                                  const void *const *xs, const void *const *bs, cudaStream_t st);
 cudaError_t launch_norm_finish(const double *partials, int n, double *out, cudaStream_t st);
 // assemble the 14 off-diagonal coefficients of every interior row (variable
 // kappa) into A (14 planes of t.astride doubles), the values the on-the-fly
@@ -167,7 +167,7 @@ constexpr int kTabulatedMaxLevel = 9;
 // Fill valsF / valsB (8 doubles per grid point each) from the FP64 row
 // tables of t, with the arithmetic of the substitutions' own evaluation.
 cudaError_t launch_tabulate(const DevTet &t, double *valsF, double *valsB, cudaStream_t st);
-constexpr int kResidualCPW = 4;  // consecutive 32-point row chunks per warp of the residual launches
+constexpr int kResidualCPW = 4;  // consecutive 32-point chunks per warp of the residual launches
 int residual_blocks(int N);  // blocks of the residual launch (8 warps of kResidualCPW row chunks each)
 int rowgrid_blocks(int N);   // blocks of the row-per-warp reductions (interior norm)
 int residual_chunks(int N);
@@ -215,12 +215,12 @@ struct PackedLaunch {
 size_t packed_smem_bytes(int reg);
 cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st);
 // Between a tet's lexicographic vectors and its packed array, over the
-// residual chunk list (tet i owns blocks [bprefix[i], bprefix[i+1]) of the
-// grid, or every block for a single tet when bprefix is null): mode 0 adds
-// the packed values to x (per tet in xs, or x1), mode 1 copies the interior
-// of x (a vector, converted to float) into the packed array.  f64: x is
-// double, else float.
-cudaError_t launch_packed_io(int mode, bool f64, const DevTet *tets, const int *bprefix, int ntets, int total_blocks,
+// residual chunk list (block i of the grid is block bmap[i].y of tet
+// bmap[i].x, or block i of tets[0] when bmap is null): mode 0 adds the packed
+// values to x (per tet in xs, or x1), mode 1 copies the interior of x (a
+// vector, converted to float) into the packed array.  Tets without a packed
+// array are skipped.  f64: x is double, else float.
+cudaError_t launch_packed_io(int mode, bool f64, const DevTet *tets, const int2 *bmap, int total_blocks,
                              void *const *xs, void *x1, cudaStream_t st);
 
 // ---- host-side views shared by the entry-point files (capi.cu defines them)

@@ -408,33 +408,26 @@ cudaError_t launch_dx(const PackedLaunch &L, size_t smem, cudaStream_t st) {
 
 // Between the lexicographic grid and the packed array, over the residual
 // chunk list (the residual launch's blocks): a warp per kResidualCPW
-// consecutive 32-point row chunks, the grid side coalesced.
+// consecutive 32-point chunks, the grid side coalesced.
 template <typename TX>
-__global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict__ tets, const int *__restrict__ bprefix,
-                                                        int n, int mode, TX *const *__restrict__ xs, TX *x1) {
-  int lo = 0;
-  if (bprefix) {
-    int hi = n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (bprefix[mid] <= (int)blockIdx.x) lo = mid;
-      else hi = mid - 1;
-    }
-  }
-  const DevTet &t = tets[lo];
-  if (!t.pk.pw) return;
+__global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict__ tets, const int2 *__restrict__ bmap,
+                                                        int mode, TX *const *__restrict__ xs, TX *x1) {
+  const int2 bm = bmap ? bmap[blockIdx.x] : make_int2(0, (int)blockIdx.x);
+  const DevTet &t = tets[bm.x];
+  float *pwv = t.pk.pw;
+  if (!pwv) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = (((int)blockIdx.x - (bprefix ? bprefix[lo] : 0)) * 8 + warp) * kResidualCPW;
-  const int N = t.N;
-  TX *x = xs ? xs[lo] : x1;
+  const int c0 = (bm.y * 8 + warp) * kResidualCPW;
+  const int N = t.N, nch = t.nchunks;
+  const int *chunks = t.chunks, *row_map = t.pk.row_map;
+  TX *x = xs ? xs[bm.x] : x1;
 #pragma unroll 1
-  for (int k = 0; k < kResidualCPW && c0 + k < t.nchunks; ++k) {
-    const int ch = t.chunks[c0 + k];
-    const int y = (ch >> 10) & 1023, z = ch >> 20, xx = 1 + 32 * (ch & 1023) + lane;
-    if (xx > N - 1 - y - z) continue;
-    const int m = t.pk.row_map[row_id(N, y, z)];
-    float *slot = t.pk.pw + packed_index((m & 0xfffff) + xx - 1, m >> 20);
-    const int64_t gi = grid_index(N, xx, y, z);
+  for (int k = 0; k < kResidualCPW && c0 + k < nch; ++k) {
+    int xx, y, z;
+    if (!chunk_point(N, chunks[c0 + k], lane, xx, y, z)) continue;
+    const int m = row_map[row_id32(N, y, z)];
+    float *slot = pwv + packed_index32((m & 0xfffff) + xx - 1, m >> 20);
+    const int gi = row_start32(N, y, z) + xx;
     if (mode == 0) x[gi] = x[gi] + (TX)*slot;
     else *slot = (float)x[gi];
   }
@@ -456,16 +449,14 @@ cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_packed_io(int mode, bool f64, const DevTet *tets, const int *bprefix, int ntets, int total_blocks,
+cudaError_t launch_packed_io(int mode, bool f64, const DevTet *tets, const int2 *bmap, int total_blocks,
                              void *const *xs, void *x1, cudaStream_t st) {
   if (total_blocks <= 0) return cudaSuccess;
   if (f64)
-    packed_io_kernel<double><<<total_blocks, 256, 0, st>>>(tets, bprefix, ntets, mode,
-                                                           reinterpret_cast<double *const *>(xs),
+    packed_io_kernel<double><<<total_blocks, 256, 0, st>>>(tets, bmap, mode, reinterpret_cast<double *const *>(xs),
                                                            reinterpret_cast<double *>(x1));
   else
-    packed_io_kernel<float><<<total_blocks, 256, 0, st>>>(tets, bprefix, ntets, mode,
-                                                          reinterpret_cast<float *const *>(xs),
+    packed_io_kernel<float><<<total_blocks, 256, 0, st>>>(tets, bmap, mode, reinterpret_cast<float *const *>(xs),
                                                           reinterpret_cast<float *>(x1));
   return cudaGetLastError();
 }

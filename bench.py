@@ -20,12 +20,13 @@ Further workloads print a line of the same form (not the default run):
                      ratio <= 3), levels U{5..8}, degrees U{4..6}, FP32,
                      kappa = 1; one step = one sweep of the whole batch (one
                      CUDA-graph replay, autotuned partition).
-  --workload serve   the request loop: Poisson arrivals (mean gap 0.5 ms) of
-                     interior solves on macro-tets of that mesh, levels 5-6
-                     (Richardson) or 5-8 (--method pcg), mixed coefficients,
-                     to 1e-8 (--method mg: levels 5-8, V(3,3) multigrid);
-                     solves/s and p50/p99 latency, beside the same requests
-                     solved one after another with FP64 sweeps.
+  --workload serve   the request loop: Poisson arrivals (mean gap --gap-ms,
+                     0.5 ms by default) of interior solves on macro-tets of
+                     that mesh, mixed coefficients, to 1e-8: by default
+                     V(3,3) multigrid on levels 5-8 (--method pcg: PCG on
+                     levels 5-8; --method richardson: smoothed Richardson on
+                     levels 5-6); solves/s and p50/p99 latency, beside the
+                     same requests solved one after another with FP64 sweeps.
   --workload smoothers  iteration counts of the surrogate ILU(0) smoother
                      against the surrogate symmetric Gauss-Seidel smoother,
                      both as Richardson smoothers and as CG preconditioners,
@@ -935,7 +936,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="default line without the level9/batch/error keys")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary"])
-    ap.add_argument("--method", default="richardson", choices=["richardson", "pcg", "mg"])
+    ap.add_argument("--method", default="mg", choices=["richardson", "pcg", "mg"], help="serve: the requests' method")
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--gap-ms", type=float, default=0.5, help="mean gap of the Poisson arrivals (serve)")
     ap.add_argument("--max-cluster", type=int, default=0, help="CTAs per cluster cap of the served set-ups")

@@ -492,8 +492,11 @@ class Server(_Handle):
         except Exception:
             pass
 
-    def submit(self, macro_tet, level, b, coeff=None, poly_degree=4, method=RICHARDSON, rtol=1e-8,
+    def submit(self, macro_tet, level, b, coeff=None, poly_degree=4, method=MG_VCYCLE, rtol=1e-8,
                max_iter=10000, x0=None, orient=ORIENT_GIVEN, boundary=BOUNDARY_V2):
+        """Queue an interior solve; returns its ticket.  The default method is
+        the V(3,3) multigrid cycle with the surrogate ILU(0) smoother: smoothed
+        Richardson alone needs hundreds to thousands of sweeps per request."""
         r = Request()
         r.macro_tet[:] = [float(v) for v in np.asarray(macro_tet, dtype=np.float64).reshape(12)]
         r.level = int(level)

@@ -649,7 +649,8 @@ ilu_status sweep(ilu_tet t, void *x, const void *b, double *d_norm_out, cudaStre
       CK(launch_packed(t->pl, st), "packed substitution launch");
     }
     Traced tr(t, 2, st);  // x += w (traced as the backward)
-    CK(launch_packed_io(0, t->precision != ILU_F32, t->d_dev, nullptr, used, nullptr, x, st), "update launch");
+    CK(launch_packed_io(0, t->precision != ILU_F32, t->d_dev, nullptr, residual_blocks(t->host.N), nullptr, x, st),
+       "update launch");
     return ILU_OK;
   }
   {

@@ -132,8 +132,9 @@ struct ConstStencil {
   }
 };
 
-// One tet: a warp per kResidualCPW consecutive 32-point chunks, 8 warps per
-// block, per-block partial norms.
+// One tet: 8 warps per block, warp w of the grid on chunks w, w + W, ... (W
+// warps in all; the launch sizes the grid to the CTAs the GPU holds at once,
+// so no partial last wave), per-block partial norms.
 template <typename TX, typename TR, typename TW, int MODE>
 __global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_kernel(
     DevTet t, const TX *__restrict__ x, const TX *__restrict__ b, TW *__restrict__ r, double *__restrict__ partials,
@@ -144,10 +145,9 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_ker
   const TR *A15 = cs.load(t.A15, sA15);
   const StencilData sd{t.Wstar, t.kappa, t.astore, t.astride};
   double acc2 = 0.0;
-  const int c0 = (blockIdx.x * 8 + warp) * kResidualCPW;  // this warp's consecutive chunks
 #pragma unroll 1
-  for (int k = 0; k < kResidualCPW && c0 + k < t.nchunks; ++k)
-    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, A15, t.N, t.chunks[c0 + k], lane, x, b, r,
+  for (int c = blockIdx.x * 8 + warp; c < t.nchunks; c += gridDim.x * 8)  // warp-uniform
+    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, A15, t.N, t.chunks[c], lane, x, b, r,
                                              packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
   // deterministic block reduction of the squared norm
 #pragma unroll
@@ -302,18 +302,27 @@ void residual_chunk_list(int N, int *out) {
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st, bool packed) {
   if (packed && (!t.pk.pw || kind == kSweepF64)) return cudaErrorInvalidValue;
-  const int nb = (t.nchunks + 8 * kResidualCPW - 1) / (8 * kResidualCPW);
-  if (nb > nblocks_cap || !t.chunks) return cudaErrorInvalidValue;
-  if (nblocks_used) *nblocks_used = nb;
-  if (nb == 0) return cudaSuccess;
-  dim3 grid(nb);
+  if (!t.chunks || nblocks_cap < 1) return cudaErrorInvalidValue;
+  const int want = (t.nchunks + 7) / 8;  // a warp per chunk
+  if (nblocks_used) *nblocks_used = 0;
+  if (want == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const int mode = t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar);
   auto go = [&](auto tx, auto tr, auto tw, auto m) {
     using TX = decltype(tx);
     using TR = decltype(tr);
     using TW = decltype(tw);
-    residual_kernel<TX, TR, TW, decltype(m)::value><<<grid, 256, 0, st>>>(t, (const TX *)x, (const TX *)b,
-                                                                          (TW *)r_out, partials, packed);
+    auto k = residual_kernel<TX, TR, TW, decltype(m)::value>;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0);
+    if (e != cudaSuccess) return;
+    // as many CTAs as are resident at once (a partial last wave would idle most SMs)
+    const int nb = std::max(1, std::min({want, nblocks_cap, std::max(1, per_sm) * sms}));
+    if (nblocks_used) *nblocks_used = nb;
+    k<<<nb, 256, 0, st>>>(t, (const TX *)x, (const TX *)b, (TW *)r_out, partials, packed);
   };
   auto by_mode = [&](auto tx, auto tr, auto tw) {
     if (mode == kOpConst) go(tx, tr, tw, std::integral_constant<int, kOpConst>{});
@@ -323,6 +332,7 @@ cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void
   if (kind == kSweepF64) by_mode(double{}, double{}, double{});
   else if (kind == kSweepMixed) by_mode(double{}, double{}, float{});
   else by_mode(float{}, float{}, float{});
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

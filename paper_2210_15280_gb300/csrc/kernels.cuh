@@ -94,7 +94,10 @@ struct LaunchStatus {
 // X = element type of x and b, R = type the residual is computed in
 enum SweepKind { kSweepF64 = 0, kSweepF32 = 1, kSweepMixed = 2 };
 
-// packed: write r into the tet's packed array (t.pk) instead of r_out
+// packed: write r into the tet's packed array (t.pk) instead of r_out.  The
+// grid holds as many CTAs as the GPU keeps resident at once (at most
+// nblocks_cap); *nblocks_used receives it, the number of partial norms
+// written to `partials`.
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st, bool packed = false);
 // How a tet's residual gets its operator: the constant stencil, assembled on

@@ -39,6 +39,8 @@ Further workloads print a line of the same form (not the default run):
                      solves to 1e-8 by V-cycle iteration and by V-cycle
                      preconditioned CG at levels 5-9, and the convergence
                      factors of the paper's Table 2 shapes measured on the GPU.
+  --workload packed  one tet at --level (default 8) on the packed kernels,
+                     FP32: ms per sweep, schedule steps and cycles per step.
   --workload boundary  convergence factors of the V(3,3)-cycle (levels 2..6)
                      with boundary variants V1 and V2 across surrogate
                      degrees: the trirectangular unit tet with kappa_i =
@@ -699,6 +701,47 @@ def mg_workload(args, g, torch):
             "levels": levels, "table2_rates_deg7_f64": rates}
 
 
+def packed_workload(args, g, torch):
+    """One tet at --level (8 by default) on the packed kernels, FP32 sweeps,
+    kappa = 1 + 0.5 sin sin sin, degree 6: ms per sweep, the schedule's steps
+    per substitution and the SM cycles per step (at the sampled clock), beside
+    the depth floor of a 384-thread CTA step from ilu_step_floor."""
+    level = args.level or 8
+    P = si.macro_tet(TET_SEED)
+    W, K = max(3, args.warmup), max(1, min(args.steps, 50))
+    t = g.Tet(P, level, coeff=g.make_coeff(*COEFF), poly_degree=DEG, precision=g.F32, kernel=g.KERNEL_PACKED)
+    b = torch.tensor(si.rhs(level, RHS_SEED), dtype=torch.float32, device="cuda")
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    t.smooth(x, b, W)
+    torch.cuda.synchronize()
+    t.profile(True)
+    t.profile_read()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = statistics.median(time_steps(t, x, b, K, flush, torch.cuda.current_stream(), torch))
+    clk = clocks.stop()
+    kms, launches = t.profile_read()
+    t.close()
+    T, _, _, _ = g.packed_schedule(level, True)
+    mhz = clk["sm_mhz"] or 2070.0
+    sub_ms = kms[1] / K  # the packed launch: both substitutions
+    floor = g.step_floor(384, 4096)
+    return {"metric": f"smoother DoF-sweeps/s (single macro-tet, level {level}, packed kernels, FP32)",
+            "value": interior(level) / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"single macro-tet L{level} ({interior(level)} interior DoF), kappa=1+0.5sin sin sin, "
+                                   "deg 6, KERNEL_PACKED", "l2": "flushed between steps (256 MiB write)"},
+            "kernel_ms_per_launch": {"residual": round(kms[0] / K, 5), "packed (both passes)": round(sub_ms, 5),
+                                     "update": round(kms[2] / K, 5)},
+            "schedule_steps_per_pass": T, "start_quantum": 1 if level <= 6 else (2 if level == 7 else 4),
+            "cycles_per_step": round(sub_ms * 1e-3 * mhz * 1e6 / (2 * T)),
+            "floor_cycles_per_step_384_threads": round(floor, 1),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
+
+
 def boundary_workload(args, g, torch):
     """Rates of the surrogate-ILU V-cycle with boundary variants V1 and V2
     against the surrogate degree (Sec. 4.2, the studies on kappa_i and on a
@@ -935,7 +978,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="default line without the level9/batch/error keys")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary"])
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "serve", "level9", "smoothers", "mg", "boundary", "packed"])
+    ap.add_argument("--level", type=int, default=0, help="packed: the tet's level (8 by default)")
     ap.add_argument("--method", default="mg", choices=["richardson", "pcg", "mg"], help="serve: the requests' method")
     ap.add_argument("--requests", type=int, default=300)
     ap.add_argument("--gap-ms", type=float, default=0.5, help="mean gap of the Poisson arrivals (serve)")
@@ -962,7 +1007,7 @@ def main():
         if rank == 0:
             line = {"batch": batch_workload, "serve": serve_workload, "level9": level9_workload,
                     "smoothers": smoothers_workload, "mg": mg_workload,
-                    "boundary": boundary_workload}[args.workload](
+                    "boundary": boundary_workload, "packed": packed_workload}[args.workload](
                 args, g, torch)
             print(json.dumps(line), flush=True)
         return

@@ -421,15 +421,41 @@ __global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict
   const int N = t.N, nch = t.nchunks;
   const int *chunks = t.chunks, *row_map = t.pk.row_map;
   TX *x = xs ? xs[bm.x] : x1;
-#pragma unroll 1
-  for (int k = 0; k < kResidualCPW && c0 + k < nch; ++k) {
-    int xx, y, z;
-    if (!chunk_point(N, chunks[c0 + k], lane, xx, y, z)) continue;
-    const int m = row_map[row_id32(N, y, z)];
-    float *slot = pwv + packed_index32((m & 0xfffff) + xx - 1, m >> 20);
-    const int gi = row_start32(N, y, z) + xx;
-    if (mode == 0) x[gi] = x[gi] + (TX)*slot;
-    else *slot = (float)x[gi];
+  // every chunk's addresses and loads first (the kernel is bound by load latency)
+  constexpr int C = kResidualCPW;
+  int gi[C], slot[C];
+  bool ok[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k) {
+    int xx = 0, y = 1, z = 1;
+    ok[k] = false;
+    if (c0 + k < nch) ok[k] = chunk_point(N, chunks[c0 + k], lane, xx, y, z);  // warp-uniform test
+    if (ok[k]) {
+      const int m = row_map[row_id32(N, y, z)];
+      slot[k] = packed_index32((m & 0xfffff) + xx - 1, m >> 20);
+      gi[k] = row_start32(N, y, z) + xx;
+    }
+  }
+  if (mode == 0) {
+    float w[C];
+    TX xo[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (ok[k]) {
+        w[k] = pwv[slot[k]];
+        xo[k] = x[gi[k]];
+      }
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (ok[k]) x[gi[k]] = xo[k] + (TX)w[k];
+  } else {
+    TX xi[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (ok[k]) xi[k] = x[gi[k]];
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (ok[k]) pwv[slot[k]] = (float)xi[k];
   }
 }
 

@@ -114,7 +114,6 @@ constexpr int residual_min_blocks() {
   return MODE == kOpStar ? 2 : 4;
 }
 
-
 // The constant stencil of a block in the residual type: FP32 coefficients
 // stay in registers, FP64 ones (30 registers) are read from shared memory.
 template <typename TR, int MODE>

@@ -313,8 +313,9 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 
 /* The row schedule the packed kernels (ILU_KERNEL_PACKED) follow for one
  * substitution at a level (the same for every tet of that level), for
- * inspection and testing.  lanes: 0 for the kernels' own lane count, else
- * 1..511 for the same construction on that many lanes; quantum: 0 for the
+ * inspection and testing.  lanes: 0 for the kernels' own lane count (384 up
+ * to level 7, 768 -- two CTAs -- at level 8), else 1..1023 for the
+ * same construction on that many lanes; quantum: 0 for the
  * kernels' start quantum at that level (1 up to level 6, 2 at 7, 4 at 8),
  * else 1, 2 or 4.  *nsteps and *lanes_out receive its size; with entries and
  * lane_off (lanes + 1 ints) non-null they receive the schedule, rows grouped
@@ -323,16 +324,18 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
  *       the quantum; the lane computes no point there) and the step lo of
  *       its first point;
  *   [1] n | y << 10 | z << 20, n the row's point count;
- *   [2] R0 | R1 << 14 | far << 28 and [3] R2 | row id << 14: R_j the word of
- *       the kernels' shared ring (384 + 8 words a step) holding producer j's
- *       value read at the first step of the 8-step block holding sw (word 384,
- *       never written, if the producer row does not exist or is read from
- *       global memory), bit j of far set for the latter;
+ *   [2] R0 | R1 << 14 | far << 28 and [3] R2 | row id << 14 | cta << 29:
+ *       R_j the word of a CTA's shared ring (384 + 8 words a step) holding
+ *       producer j's value read at the first step of the 8-step block holding
+ *       sw (word 384, never written, if the producer row does not exist or is
+ *       read from global memory), bit j of far set for the latter, bit j of
+ *       cta the CTA whose ring it is (lane / 384; the consumer's own CTA for
+ *       word 384);
  *   [4] the row coordinate (2x - (N - y - z)) / (2N) of step sw's point
  *       (float bits; x = 0 forward, n + lo - sw backward);
  *   [5..7] the producer codes: mode in bits 30-31 (0 no such interior row,
  *       1 read from the ring, 2 read from global memory), the producer's lane
- *       in bits 0-8, and in bits 9-29 the step distance k0 of the first value
+ *       in bits 0-9, and in bits 10-29 the step distance k0 of the first value
  *       the consumer reads (the producer's value at step tau + 1 - k0 is its
  *       second value at step tau).
  * Forward producers of row (y, z): (y-1, z), (y, z-1), (y+1, z-1); backward:

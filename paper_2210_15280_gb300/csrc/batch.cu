@@ -74,7 +74,7 @@ struct Group {
 // quantum: one launch, a CTA per tet, longest tets first (their CTAs start
 // first).
 struct PackedGroup {
-  int dxp = 0, reg = 0, q = 1;
+  int dxp = 0, reg = 0, q = 1, cl = 1;
   bool v1 = false;
   std::vector<int> members;  // tet indices, most steps first
   PackedLaunch pl = {};
@@ -174,7 +174,8 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
   // rows in registers, rows in shared memory, tabulated values
   auto cls = [](const TetView &v) { return v.reg >= 0 ? 1 : (v.reg == kWaveTabulated ? 2 : 0); };
   std::map<std::tuple<int, int, int>, int> key;
-  std::map<std::pair<int, int>, int> pkey;  // packed tets by table layout and start quantum
+  std::map<std::pair<int, int>, int> pkey;  // packed tets by table layout and start quantum (which
+                                            // also fixes the cluster size)
   for (int i = 0; i < n; ++i) {
     const TetView &v = b->views[i];
     if (v.packed) {
@@ -200,6 +201,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       PackedGroup &pg = b->pgroups[pkey[std::make_pair(v.rstride, v.packed_q)]];
       pg.dxp = v.rstride;
       pg.q = v.packed_q;
+      pg.cl = v.packed_cl;
       pg.reg = v.dx <= 3 ? 3 : 6;  // the degree of the tets' packed tables (zero padded, as their own launches)
       pg.v1 = pg.v1 || v.dev->bnd != nullptr;
       pg.members.push_back(i);
@@ -342,6 +344,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       L.ntets = (int)pg.members.size();
       L.reg = pg.reg;
       L.q = pg.q;
+      L.cl = pg.cl;
       L.v1 = pg.v1;
       at += pg.members.size();
       BK(cudaStreamCreateWithFlags(&pg.st, cudaStreamNonBlocking), "cudaStreamCreate");

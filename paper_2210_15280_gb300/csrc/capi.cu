@@ -374,12 +374,14 @@ ilu_status upload_packed(ilu_tet t) {
   p.row_map = base + 16 * ne + lanes + 1;
   p.pw = t->d_pkw;
   p.nsteps = pl->nsteps;
+  p.lanes = pl->lanes;
   PackedLaunch &L = t->pl;
   L.tets = t->d_dev;
   L.order = nullptr;
   L.ntets = 1;
   L.reg = packed_degree(t->host.dx);
   L.q = pl->q;
+  L.cl = pl->lanes / kPackedLanes;
   L.v1 = t->host.boundary == ILU_BOUNDARY_V1;
   return ILU_OK;
 }
@@ -773,6 +775,7 @@ bool tet_view(ilu_tet t, TetView *v) {
   v->packed = t->use_packed;
   v->packed_steps = t->use_packed ? 2 * t->dev.pk.nsteps : 0;
   v->packed_q = t->use_packed ? t->pl.q : 0;
+  v->packed_cl = t->use_packed ? t->pl.cl : 0;
   return true;
 }
 WaveGeom wave_geom(int N, int kind, int dxp, int reg, bool fwd, int requested) {
@@ -1181,16 +1184,17 @@ ilu_status ilu_packed_schedule(int level, int forward, int lanes, int quantum, i
                                int *entries, int *lane_off) {
   if (!nsteps || !lanes_out) return fail(ILU_EINVAL, "null argument");
   if (level < 2 || level > kPackedMaxLevel) return fail(ILU_EINVAL, "the packed schedules cover levels 2 to 8");
-  if (lanes < 0 || lanes > 511) return fail(ILU_EINVAL, "lanes must be 0 (the kernels' count) or 1..511");
+  if (lanes < 0 || lanes > 1023) return fail(ILU_EINVAL, "lanes must be 0 (the kernels' count) or 1..1023");
   if (quantum != 0 && quantum != 1 && quantum != 2 && quantum != 4)
     return fail(ILU_EINVAL, "quantum must be 0 (the kernels' own), 1, 2 or 4");
   const int N = 1 << level, q = quantum ? quantum : packed_quantum(N);
   std::string err;
   PackedPlan own;
   const PackedPlan *p = nullptr;
-  if ((lanes == 0 || lanes == kPackedLanes) && q == packed_quantum(N)) {
+  const int own_lanes = packed_cluster(N) * kPackedLanes;
+  if ((lanes == 0 || lanes == own_lanes) && q == packed_quantum(N)) {
     p = packed_plan_cached(N, &err);
-  } else if (make_packed_plan(N, lanes ? lanes : kPackedLanes, q, &own, &err)) {
+  } else if (make_packed_plan(N, lanes ? lanes : own_lanes, q, &own, &err)) {
     p = &own;
   }
   if (!p) return fail(ILU_EINVAL, err);

@@ -34,6 +34,7 @@ struct StencilData {
   const double *Wstar, *kappa;
   const void *astore;  // stored off-diagonal coefficients (MODE 2)
   int64_t astride;
+  int plane;           // lanes of the packed array (when r goes there)
 };
 
 // MODE of the operator (kernels.cuh): constant stencil, assembled on the fly
@@ -101,7 +102,7 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, const TR 
   }
   if (pmap) {
     const int m = pmap[row_id32(N, y, z)];
-    pw[packed_index32((m & 0xfffff) + xx - 1, m >> 20)] = (float)res;
+    pw[packed_index32((m & 0xfffff) + xx - 1, m >> 20, t.plane)] = (float)res;
   } else {
     r[R.r0 + xx] = (TW)res;
   }
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_ker
   __shared__ TR sA15[15];
   ConstStencil<TR, MODE> cs;
   const TR *A15 = cs.load(t.A15, sA15);
-  const StencilData sd{t.Wstar, t.kappa, t.astore, t.astride};
+  const StencilData sd{t.Wstar, t.kappa, t.astore, t.astride, t.pk.lanes};
   double acc2 = 0.0;
 #pragma unroll 1
   for (int c = blockIdx.x * 8 + warp; c < t.nchunks; c += gridDim.x * 8)  // warp-uniform
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>())
   const int nch = tg.nchunks;
   const int *chunks = tg.chunks;
   TW *r = reinterpret_cast<TW *>(tg.w);
-  const StencilData sd{tg.Wstar, tg.kappa, tg.astore, tg.astride};
+  const StencilData sd{tg.Wstar, tg.kappa, tg.astore, tg.astride, tg.pk.lanes};
   const int *pmap = tg.pk.pw ? tg.pk.row_map : nullptr;
   float *pw = tg.pk.pw;
   const TX *xv = xs[bm.x], *bv = bs[bm.x];

@@ -46,6 +46,7 @@ struct PackedDev {
   const int *row_map;
   float *pw;
   int nsteps;
+  int lanes;  // lanes of the schedule: kPackedLanes per CTA of the tet's cluster
 };
 
 // Everything a kernel needs to know about one tet.  Plain old data so that it
@@ -213,6 +214,7 @@ struct PackedLaunch {
   int ntets;
   int reg;  // degree of the row tables (3 or 6)
   int q;    // the schedules' start quantum (1, 2 or 4; the same for every tet of the launch)
+  int cl;   // CTAs per tet (1 or 2; the same for every tet of the launch)
   bool v1;
 };
 size_t packed_smem_bytes(int reg);
@@ -238,6 +240,7 @@ struct TetView {
   bool packed;  // its substitutions run on the packed kernels (cost: steps of both passes)
   int packed_steps;
   int packed_q;  // their schedules' start quantum
+  int packed_cl; // and CTAs per tet
 };
 bool tet_view(ilu_tet_s *t, TetView *v);
 // partition of one substitution (requested > 0: about that many slabs)

@@ -76,6 +76,35 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 
 __device__ __forceinline__ int pmode(int code) { return (code >> 30) & 3; }
 
+// cluster primitives: this CTA's rank, the cluster-window address of a
+// shared location in CTA `rank`, a load through that window, and a barrier of
+// every thread of the cluster (release / acquire: shared-memory writes before
+// it are visible to every CTA after it)
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_addr(const void *p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+  return a;
+}
+__device__ __forceinline__ float ld_cluster(unsigned a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the barrier of a packed pass: the CTA's, or the cluster's for CL > 1
+template <int CL>
+__device__ __forceinline__ void pass_sync() {
+  if constexpr (CL > 1) cluster_sync_all();
+  else __syncthreads();
+}
+
 // One substitution of one tet on one CTA.
 //
 // Lane state: the current row (its points' steps [lo, lo + n), the ring word
@@ -112,14 +141,17 @@ __device__ __forceinline__ int pmode(int code) { return (code >> 30) & 3; }
 // are mirrored after row RG - 1 so that a producer's reads within a block
 // never wrap.  Inputs are read and results written four steps at a time (one
 // 16-byte block per lane).
-template <bool FWD, int DX, bool V1, int Q>
+template <bool FWD, int DX, bool V1, int Q, int CL>
 __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem) {
   constexpr int SF2 = 4 * (DX + 1);  // float2 of a staged row: coefficient k of the four function pairs
   float *ring = reinterpret_cast<float *>(smem);                 // [RR][RW]
   float4 *q = reinterpret_cast<float4 *>(ring + RR * RW);        // [QS][LN] far producer values (.y .z .w)
   int4 *sent = reinterpret_cast<int4 *>(q + QS * LN);            // [LN][2]
   float2 *stage = reinterpret_cast<float2 *>(sent + 2 * LN);     // [LN][SF2]
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x;                                    // this CTA's lane (stage, sent)
+  const unsigned rank = CL > 1 ? cluster_rank() : 0u;
+  const int lg = (int)rank * LN + lane;                            // the schedule's lane
+  const int LT = CL * LN;                                          // lanes of the schedule and the packed array
   const int N = t.N;
   const int4 *ent = FWD ? t.pk.ent_f : t.pk.ent_b;  // entry e at ent[2e], ent[2e + 1]
   const int *off = t.pk.off;
@@ -134,10 +166,10 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     float4 *r4 = reinterpret_cast<float4 *>(ring);
     for (int i = lane; i < RR * RW / 4; i += LN) r4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  __syncthreads();
+  pass_sync<CL>();  // every CTA's ring is clear before any lane of the cluster reads one
 
-  const int e_end = off[lane + 1];
-  int e_nx = off[lane];  // index of the next row's entry
+  const int e_end = off[lg + 1];
+  int e_nx = off[lg];  // index of the next row's entry
   int4 nxa = make_int4(0, 0, 0, 0), nxb = make_int4(0, 0, 0, 0);  // the next row's entry
   int ev = INT_MAX;  // the next row's switch step (its cursor event is kPackedPre steps earlier)
   if (e_nx < e_end) {
@@ -151,7 +183,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   // the block's elements in reverse order)
   auto ppos = [&](int s) { return FWD ? s : T - 1 - s; };
   auto block = [&](int g) {
-    return reinterpret_cast<float4 *>(pw) + (size_t)(FWD ? g : (T >> 2) - 1 - g) * LN + lane;
+    return reinterpret_cast<float4 *>(pw) + (size_t)(FWD ? g : (T >> 2) - 1 - g) * LT + lg;
   };
 
   // prefetch cursor: the far producers of the row this lane works on
@@ -164,14 +196,14 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     const int lo = (nxa.x & 0xffff) + (nxa.x >> 16);
     pf_end = lo + (nxa.y & 1023) - 1;
     auto pos0 = [&](int code) {  // the value read at step tau2
-      return (int)packed_index(ppos(tau2 - ((code >> 9) & 0x1fffff) + 1), code & 511);
+      return packed_index32(ppos(tau2 - ((code >> 10) & 0xfffff) + 1), code & 1023, LT);
     };
     if (pgm) {
       o0 = pos0(nxb.y);
       o1 = pos0(nxb.z);
       o2 = pos0(nxb.w);
     }
-    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)(nxa.w >> 14) * SF2);
+    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)(((unsigned)nxa.w >> 14) & 0x7fffu) * SF2);
     float4 *dst = reinterpret_cast<float4 *>(my_stage);
 #pragma unroll
     for (int i = 0; i < SF2 / 2; ++i) cpa16(dst + i, src + i);
@@ -182,8 +214,8 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   };
   // the next value of a far producer (position offset o, one step on)
   auto next_pos = [&](int &o) {
-    if (FWD) o += (o & 3) == 3 ? 4 * LN - 3 : 1;
-    else o -= (o & 3) == 0 ? 4 * LN - 3 : 1;
+    if (FWD) o += (o & 3) == 3 ? 4 * LT - 3 : 1;
+    else o -= (o & 3) == 0 ? 4 * LT - 3 : 1;
   };
   auto prefetch = [&](int tau2) {  // one commit group per step
     if (pgm && tau2 <= pf_end) {
@@ -207,6 +239,10 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   int lo = 0, cn = 0, c_y = 0, c_z = 0;
   int gm = 0;                       // bit j: producer j comes through the queue
   int B0 = LN, B1 = LN, B2 = LN;    // ring word of each producer's read at the block's first step
+  // CL > 1: cluster-window base of each producer's ring; until the lane's
+  // first row, its own ring (the reads give the column nothing writes)
+  unsigned A0 = 0, A1 = 0, A2 = 0;
+  if constexpr (CL > 1) A0 = A1 = A2 = cluster_addr(ring, rank);
   float cv0 = 0.f, cv1 = 0.f, cv2 = 0.f;  // each producer's value of the last step
   float v1 = 0.f;                         // this lane's value of the last step
   float2 t2 = make_float2(0.f, 0.f);
@@ -227,6 +263,12 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     B1 = (nxa.z >> 14) & 0x3fff;
     B2 = nxa.w & 0x3fff;
     gm = (nxa.z >> 28) & 7;
+    if constexpr (CL > 1) {
+      const unsigned cta = (unsigned)nxa.w >> 29;
+      A0 = cluster_addr(ring, cta & 1);
+      A1 = cluster_addr(ring, (cta >> 1) & 1);
+      A2 = cluster_addr(ring, (cta >> 2) & 1);
+    }
     const float tt = __int_as_float(nxb.x);
     t2 = make_float2(tt, tt);
     const float4 *sv = reinterpret_cast<const float4 *>(my_stage);
@@ -256,7 +298,16 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     if (((J + PD) & (Q - 1)) == Q - 1 && tau + PD == ev) cursor(tau + PD);
     prefetch(tau + PD);
     // each producer's second value of this step
-    float r0 = ring[B0 + J * RW], r1 = ring[B1 + J * RW], r2 = ring[B2 + J * RW];
+    float r0, r1, r2;
+    if constexpr (CL > 1) {
+      r0 = ld_cluster(A0 + 4u * (unsigned)(B0 + J * RW));
+      r1 = ld_cluster(A1 + 4u * (unsigned)(B1 + J * RW));
+      r2 = ld_cluster(A2 + 4u * (unsigned)(B2 + J * RW));
+    } else {
+      r0 = ring[B0 + J * RW];
+      r1 = ring[B1 + J * RW];
+      r2 = ring[B2 + J * RW];
+    }
     if (gm) {
       const float4 qv = q[J * LN + lane];
       if (gm & 1) r0 = qv.y;
@@ -331,7 +382,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     v1 = out;
     ring[wb + J * RW] = out;
     if (mir) ring[(RG + J) * RW + lane] = out;
-    if ((J & (Q - 1)) == Q - 1) __syncthreads();  // every Q steps (producers are at least Q + 1 steps ahead)
+    if ((J & (Q - 1)) == Q - 1) pass_sync<CL>();  // every Q steps (producers are at least Q + 1 steps ahead)
     return out;
   };
 
@@ -371,37 +422,58 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     if (B2 >= RG * RW) B2 -= RG * RW;
   }
   cpa_wait<0>();
-  __syncthreads();
+  pass_sync<CL>();  // no CTA clears its ring for the next pass while another still reads it
 }
 
-template <int DX, bool V1, int Q>
+// one cluster of CL CTAs per tet (CL consecutive blocks)
+template <int DX, bool V1, int Q, int CL>
 __global__ void __launch_bounds__(kPackedLanes, 1) packed_kernel(const DevTet *__restrict__ tets,
                                                                  const int *__restrict__ order) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int ti = order ? order[blockIdx.x] : (int)blockIdx.x;
+  const int b = (int)blockIdx.x / CL;
+  const int ti = order ? order[b] : b;
   const DevTet &t = tets[ti];
-  packed_pass<true, DX, V1, Q>(t, smem);
-  packed_pass<false, DX, V1, Q>(t, smem);
+  packed_pass<true, DX, V1, Q, CL>(t, smem);
+  packed_pass<false, DX, V1, Q, CL>(t, smem);
 }
 
-template <int DX, bool V1, int Q>
+template <int DX, bool V1, int Q, int CL>
 cudaError_t launch_one(const PackedLaunch &L, size_t smem, cudaStream_t st) {
-  auto k = packed_kernel<DX, V1, Q>;
+  auto k = packed_kernel<DX, V1, Q, CL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<L.ntets, kPackedLanes, smem, st>>>(L.tets, L.order);
+  if constexpr (CL == 1) {
+    k<<<L.ntets, kPackedLanes, smem, st>>>(L.tets, L.order);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.ntets * CL);
+    cfg.blockDim = dim3(kPackedLanes);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, L.tets, L.order);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
 template <int DX>
 cudaError_t launch_dx(const PackedLaunch &L, size_t smem, cudaStream_t st) {
-  switch (L.q * 2 + (L.v1 ? 1 : 0)) {
-    case 2: return launch_one<DX, false, 1>(L, smem, st);
-    case 3: return launch_one<DX, true, 1>(L, smem, st);
-    case 4: return launch_one<DX, false, 2>(L, smem, st);
-    case 5: return launch_one<DX, true, 2>(L, smem, st);
-    case 8: return launch_one<DX, false, 4>(L, smem, st);
-    case 9: return launch_one<DX, true, 4>(L, smem, st);
+  // the schedules: quantum 1 (up to level 6) and 2 (level 7) on one CTA,
+  // quantum 4 on a cluster of two (level 8)
+  switch (L.q * 4 + L.cl * 2 + (L.v1 ? 1 : 0) - 2) {
+    case 4: return launch_one<DX, false, 1, 1>(L, smem, st);
+    case 5: return launch_one<DX, true, 1, 1>(L, smem, st);
+    case 8: return launch_one<DX, false, 2, 1>(L, smem, st);
+    case 9: return launch_one<DX, true, 2, 1>(L, smem, st);
+    case 18: return launch_one<DX, false, 4, 2>(L, smem, st);
+    case 19: return launch_one<DX, true, 4, 2>(L, smem, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -432,7 +504,7 @@ __global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict
     if (c0 + k < nch) ok[k] = chunk_point(N, chunks[c0 + k], lane, xx, y, z);  // warp-uniform test
     if (ok[k]) {
       const int m = row_map[row_id32(N, y, z)];
-      slot[k] = packed_index32((m & 0xfffff) + xx - 1, m >> 20);
+      slot[k] = packed_index32((m & 0xfffff) + xx - 1, m >> 20, t.pk.lanes);
       gi[k] = row_start32(N, y, z) + xx;
     }
   }

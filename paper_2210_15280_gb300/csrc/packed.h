@@ -1,14 +1,14 @@
 // packed.h -- the packed substitution kernels of the FP32 sweeps (packed.cu)
 // and their host-side row schedules (packed_plan.cpp).
 //
-// A packed launch gives every macro-tetrahedron one CTA of kPackedLanes
-// threads, which runs the tet's whole forward substitution and then its whole
-// backward substitution (Alg. 2 of arXiv 2210.15280) without waiting on any
-// other CTA.  Inside the CTA the interior rows (y, z) are packed onto the
-// lanes: a lane owns one row at a time, keeps that row's surrogate
-// polynomials in registers and computes one point of it per step; the CTA
-// meets at a block barrier every q steps (q, the schedule's quantum: 1, 2 or
-// 4 by level).
+// A packed launch gives every macro-tetrahedron one cluster of c CTAs of
+// kPackedLanes threads each (c = 1 up to level 7, 2 at level 8), which
+// runs the tet's whole forward substitution and then its whole backward
+// substitution (Alg. 2 of arXiv 2210.15280) without waiting on any other
+// cluster.  The interior rows (y, z) are packed onto the cluster's lanes: a
+// lane owns one row at a time, keeps that row's surrogate polynomials in
+// registers and computes one point of it per step; the cluster meets at a
+// barrier every q steps (q, the schedule's quantum: 1, 2 or 4 by level).
 //
 // The schedule -- which lane owns which row from which step on -- is computed
 // on the host once per level (packed_plan.cpp): a list schedule that starts
@@ -20,9 +20,9 @@
 // reversed schedule is valid, and every row stays on its lane.
 //
 // Packed layout.  Point (x, y, z) of a row that starts at forward step s on
-// lane l has the slot (s + x - 1, l) of a float array of T steps x
-// kPackedLanes lanes in four-step blocks: step s of lane l at
-// ((s / 4) * kPackedLanes + l) * 4 + s % 4 (packed_index).  The residual
+// lane l has the slot (s + x - 1, l) of a float array of T steps x n lanes
+// (n: the cluster's lanes) in four-step blocks: step s of lane l at
+// ((s / 4) * n + l) * 4 + s % 4 (packed_index32).  The residual
 // writes r there, the forward pass replaces it by its result and the
 // backward pass by its own; an update kernel adds the latter to x.  The
 // passes move one 16-byte block per lane every four steps, the lanes of a warp
@@ -44,9 +44,10 @@ constexpr int kPackedMaxLevel = 8; // highest level the packed kernels take
 constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fill the shared memory)
 
 // A producer code tells a consumer row where the values of one of its three
-// producer rows are (bits 30-31 the mode): the producer's lane in bits 0-8,
-// the step distance k0 of the first value the consumer reads at a step (the
-// second is written one step later) in bits 9-29, and
+// producer rows are (bits 30-31 the mode): the producer's lane (over the
+// whole cluster) in bits 0-9, the step distance k0 of the first value the
+// consumer reads at a step (the second is written one step later) in bits
+// 10-29, and
 //   kProdNone    no such interior row (read from the ring column nothing
 //                writes: 0);
 //   kProdRing    k0 <= min(kPackedRing - 1, kPackedRing + 1 - q): read from
@@ -54,36 +55,34 @@ constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fil
 //   kProdGlobal  further behind: read back from the packed array in global
 //                memory, prefetched like the inputs.
 enum { kProdNone = 0, kProdRing = 1, kProdGlobal = 2 };
-inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 9); }
+inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 10); }
 
 // One row of a schedule (32 bytes), in the pass's own steps:
 //   sw_dlo  sw | (lo - sw) << 16: the switch step sw (q - 1 mod q) and the
 //           step lo of the row's first point (lo - sw in 1..q);
 //   nyz     n | y << 10 | z << 20 (n = points of the row);
-//   r01g    R0 | R1 << 14 | far << 28, r2rid R2 | row id << 14: R_j is the
-//           ring word of producer j's value read at the first step of the
-//           kPackedBlock-step block holding sw (kPackedLanes if the producer
-//           row does not exist or comes through the queue), bit j of far set
-//           if producer j comes through the queue;
+//   r01g    R0 | R1 << 14 | far << 28, r2rid R2 | row id << 14 | cta << 29:
+//           R_j is the word, in the ring of the CTA holding producer j, of
+//           the value read at the first step of the kPackedBlock-step block
+//           holding sw (kPackedLanes if the producer row does not exist or
+//           comes through the queue), bit j of far set if producer j comes
+//           through the queue, bit j of cta the CTA (cluster rank) of its lane;
 //   tt0     the row coordinate t of the point at step sw (float bits);
 //   p[3]    the three producer codes.
 struct PackedEntry {
   int sw_dlo, nyz, r01g, r2rid, tt0, p[3];
 };
 
-// slot of step s, lane l in the packed array
+// slot of step s, lane l in the packed array of `lanes` lanes
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
-inline size_t packed_index(int s, int l) { return ((size_t)(s >> 2) * kPackedLanes + l) * 4 + (s & 3); }
-#if defined(__CUDACC__)
-__host__ __device__
-#endif
-inline int packed_index32(int s, int l) { return (((s >> 2) * kPackedLanes + l) << 2) + (s & 3); }
+inline int packed_index32(int s, int l, int lanes) { return (((s >> 2) * lanes + l) << 2) + (s & 3); }
 
 struct PackedPlan {
-  int N = 0, lanes = 0, q = 1, nsteps = 0;  // q: the start quantum; nsteps = T, the steps of either pass
-                                            // (a multiple of kPackedBlock)
+  int N = 0, lanes = 0, q = 1, nsteps = 0;  // lanes: kPackedLanes per CTA of the cluster; q: the start
+                                            // quantum; nsteps = T, the steps of either pass (a multiple of
+                                            // kPackedBlock)
   std::vector<PackedEntry> fwd, bwd;  // grouped by lane, each lane's rows in step order
   std::vector<int> lane_off;          // lanes + 1 offsets into either list
   std::vector<int> row_map;           // per row id: forward first step | lane << 20
@@ -94,11 +93,13 @@ struct PackedPlan {
 // (y-1, z), (y, z-1), (y+1, z-1); the backward ones (y+1, z), (y, z+1),
 // (y-1, z+1).  False (with err) if a check of the schedule fails.
 bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err);
-// The start quantum of the kernels' schedules at N.
+// The start quantum and the cluster size (CTAs per tet) of the kernels'
+// schedules at N.
 int packed_quantum(int N);
-// The plan on kPackedLanes lanes with the level's quantum, computed once per
-// level and kept for the life of the process; null (with err) if the
-// schedule fails.
+int packed_cluster(int N);
+// The plan on packed_cluster(N) x kPackedLanes lanes with the level's
+// quantum, computed once per level and kept for the life of the process;
+// null (with err) if the schedule fails.
 const PackedPlan *packed_plan_cached(int N, std::string *err);
 
 }  // namespace ilu

@@ -36,9 +36,14 @@ def decode(e):
     sw, lo = w[0] & 0xffff, (w[0] & 0xffff) + (w[0] >> 16)
     n, y, z = w[1] & 1023, (w[1] >> 10) & 1023, w[1] >> 20
     R = [w[2] & 0x3fff, (w[2] >> 14) & 0x3fff, w[3] & 0x3fff]
-    gm, rid = (w[2] >> 28) & 7, w[3] >> 14
+    gm, rid, cta = (w[2] >> 28) & 7, (w[3] >> 14) & 0x7fff, w[3] >> 29
     tt0 = float(np.array([w[4]], dtype=np.uint32).view(np.float32)[0])
-    return dict(sw=sw, lo=lo, n=n, y=y, z=z, codes=w[5:8], R=R, gm=gm, rid=rid, tt0=tt0)
+    return dict(sw=sw, lo=lo, n=n, y=y, z=z, codes=w[5:8], R=R, gm=gm, rid=rid, cta=cta, tt0=tt0)
+
+
+def lane_k0(c):
+    """the producer's lane and the step distance k0 of a producer code"""
+    return c & 1023, (c >> 10) & 0xfffff
 
 
 def mode(c):
@@ -47,6 +52,10 @@ def mode(c):
 
 def quantum_of(level):
     return 1 if level <= 6 else (2 if level == 7 else 4)
+
+
+def lanes_of(level):
+    return LANES if level <= 7 else 2 * LANES
 
 
 def emulate_pass(N, T, lanes, rows, forward, Ls, Dinv, point_id, pw, B=1):
@@ -111,7 +120,7 @@ def emulate_pass(N, T, lanes, rows, forward, Ls, Dinv, point_id, pw, B=1):
             for j in range(3):
                 if mode(codes[j]) != 2:
                     continue
-                slot, k0 = codes[j] & 511, (codes[j] >> 9) & 0x1fffff
+                slot, k0 = lane_k0(codes[j])
                 e = pw[(prow(t2 - k0 + 1), slot)]
                 if e[2] == tag:  # written in this pass: stored at the end of its four-step block
                     assert (e[3] | 3) + 1 <= tau, "far value read before it was stored"
@@ -134,7 +143,7 @@ def emulate_pass(N, T, lanes, rows, forward, Ls, Dinv, point_id, pw, B=1):
             for j in range(3):
                 md = mode(codes[j])
                 if md == 1:
-                    slot, k0 = codes[j] & 511, (codes[j] >> 9) & 0x1fffff
+                    slot, k0 = lane_k0(codes[j])
                     w, g0 = tau - k0 + 1, tau - tau % B
                     assert w < g0, "ring value read in the group of steps that wrote it"
                     assert w + RING > g0 + B - 1, "ring row rewritten within the reading group"
@@ -192,13 +201,14 @@ def emulate_pass(N, T, lanes, rows, forward, Ls, Dinv, point_id, pw, B=1):
 
 
 @pytest.mark.parametrize("level,lanes,quantum", [(3, 0, 0), (4, 0, 0), (5, 0, 0), (5, 24, 0), (6, 48, 0), (6, 0, 0),
-                                                (4, 0, 2), (5, 24, 4), (6, 48, 2), (6, 40, 4)])
+                                                (4, 0, 2), (5, 24, 4), (6, 48, 2), (6, 40, 4), (6, 700, 4)])
 def test_emulated_schedule_sweep_equals_the_oracle(g, orc, level, lanes, quantum):
     """Level 3-6 on the kernels' 384 lanes and on few lanes (which forces
     long delays and far producers read from global memory), with the
     kernels' start quantum and with quanta 2 and 4 (the level-7 and level-8
-    kernels' row padding, switch steps and barrier groups): the emulated
-    sweep equals the oracle's sweep to FP64 rounding."""
+    kernels' row padding, switch steps and barrier groups), and on 700 lanes
+    (lane numbers of a two-CTA cluster): the emulated sweep equals the
+    oracle's sweep to FP64 rounding."""
     P = si.macro_tet(60 + level)
     co = orc.Coeff("sinprod", 1.0, 0.5)
     pr = orc.Problem(P, level, co, deg=[3, 3, 3])
@@ -233,8 +243,8 @@ def test_emulated_schedule_sweep_equals_the_oracle(g, orc, level, lanes, quantum
         x[orc.index(N, *p)] += v
     assert np.abs(x - want).max() <= 1e-12 * np.abs(want).max()
     far = sum(int(mode(int(c) & 0xffffffff) == 2) for e in np.concatenate([ent_f, ent_b]) for c in e[5:8])
-    if lanes and level >= 6:
-        assert far > 0  # the run exercised the global-memory path
+    if 0 < lanes < LANES and level >= 6:
+        assert far > 0  # few lanes: the run exercised the global-memory path
 
 
 @pytest.mark.parametrize("level", [5, 6, 7, 8])
@@ -250,7 +260,7 @@ def test_schedule_covers_every_row_once(g, orc, level):
     q = quantum_of(level)
     T, ln, ef, off = g.packed_schedule(level, True)
     _, _, eb, _ = g.packed_schedule(level, False)
-    assert T % BLOCK == 0
+    assert T % BLOCK == 0 and ln == lanes_of(level)
     ring_max = min(RING - 1, RING + 1 - q)
     for fwd, ent in ((True, ef), (False, eb)):
         rows = [decode(e) for e in ent]
@@ -263,9 +273,12 @@ def test_schedule_covers_every_row_once(g, orc, level):
             assert r["tt0"] == np.float32((2 * x_sw - K) * (0.5 / N))
             tau0 = r["sw"] & ~(BLOCK - 1)
             for j, c in enumerate(r["codes"]):
-                md, lane_p, k0 = mode(c), c & 511, (c >> 9) & 0x1fffff
+                md = mode(c)
+                lane_p, k0 = lane_k0(c)
                 if md == 1:
-                    assert q + 1 <= k0 <= ring_max and r["R"][j] == ((tau0 + 1 - k0) % RING) * RW + lane_p
+                    assert q + 1 <= k0 <= ring_max
+                    assert r["R"][j] == ((tau0 + 1 - k0) % RING) * RW + lane_p % LANES
+                    assert ((r["cta"] >> j) & 1) == lane_p // LANES  # the ring of the producer's CTA
                 else:
                     assert r["R"][j] == LANES and (k0 > ring_max if md == 2 else k0 == 0)
                 assert ((r["gm"] >> j) & 1) == (md == 2)
@@ -273,6 +286,9 @@ def test_schedule_covers_every_row_once(g, orc, level):
             prev = None
             for e in ent[off[l]:off[l + 1]]:
                 r = decode(e)
+                for j, c in enumerate(r["codes"]):
+                    if mode(c) != 1:  # no ring producer: the consumer's own CTA (its zero column)
+                        assert ((r["cta"] >> j) & 1) == l // LANES
                 if prev is not None:
                     assert r["sw"] >= prev["lo"] + prev["n"]          # the step after a row has no point
                     assert r["sw"] >= prev["sw"] + PRE + 1            # the stage is free for the copy

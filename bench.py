@@ -330,6 +330,7 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None, compact=False):
     nbytes = sum(v.numel() for v in xs) * 4
     achieved = idof * 24 / (total_ms / K / 1e3) / 1e9  # F32 sweep: 24 algorithmic bytes per DoF (this rank)
     hbm, src = peaks()
+    launches = B.launches_per_sweep() * K
     per_tet = None
     if world == 1:
         per_tet = one_by_one(g, torch, tets, xs, bs, mesh, levels, degs, W, min(K, 5))
@@ -354,7 +355,7 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None, compact=False):
                        "tuned": "packed kernels, longest tets first", "l2": "inputs larger than L2",
                        "parallelism": f"tets sharded over {world} GPU(s), no exchange"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": None,
+            "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": None, "kernel": "whole sweep (residual + forward + backward)", "peak_source": src},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],

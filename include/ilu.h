@@ -393,13 +393,21 @@ ilu_status ilu_batch_destroy(ilu_batch b);
 /* `sweeps` sweeps of Alg. 2 on every tet of the batch: x[i], b[i] (host
  * arrays of n device pointers) are tet i's full-grid vectors, as for
  * ilu_smooth.  A pass is one residual launch over all tets and, per group of
- * tets with equal level and row layout, one forward and one backward launch;
- * the groups' launches run concurrently.  The passes are captured in a CUDA
+ * tets on the slab kernels with equal level and row layout, one forward and
+ * one backward launch; per group of tets on the packed kernels with equal row
+ * layout and start quantum, one launch of both substitutions, and after them
+ * one update launch x += w over all packed tets; the groups' launches run
+ * concurrently.  The passes are captured in a CUDA
  * graph on the first call (again when `sweeps` changes) and replayed on
  * `stream`.  Synchronises `stream` before returning, to report a timed-out
  * wait (ILU_ETIMEOUT, the batch is then failed and must be destroyed).
  * Results equal ilu_smooth on each tet, bit for bit. */
 ilu_status ilu_batch_smooth(ilu_batch bt, void *const *x, const void *const *b, int sweeps, void *stream);
+
+/* The number of kernels one sweep of ilu_batch_smooth launches (residual
+ * launches, group launches and the packed update launch), into *per_sweep.
+ * ILU_EINVAL for a null argument. */
+ilu_status ilu_batch_launches(ilu_batch bt, int *per_sweep);
 
 /* ------------------------------------------------------------- multigrid -- */
 

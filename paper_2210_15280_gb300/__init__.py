@@ -34,7 +34,7 @@ EXPORTS = [
     "ilu_opts_default", "ilu_setup", "ilu_destroy", "ilu_import_surrogate", "ilu_export_surrogate",
     "ilu_surrogate_size", "ilu_eval_surrogate", "ilu_exact_factor", "ilu_stencil", "ilu_smooth",
     "ilu_smooth_host", "ilu_residual", "ilu_solve", "ilu_batch_create", "ilu_batch_destroy",
-    "ilu_batch_smooth", "ilu_server_create", "ilu_server_submit", "ilu_server_wait", "ilu_server_release",
+    "ilu_batch_smooth", "ilu_batch_launches", "ilu_server_create", "ilu_server_submit", "ilu_server_wait", "ilu_server_release",
     "ilu_server_stats", "ilu_server_destroy", "ilu_num_nodes", "ilu_num_interior", "ilu_index",
     "ilu_last_error", "ilu_version", "ilu_profile_enable", "ilu_profile_read", "ilu_residual_noalloc",
     "ilu_mg_setup", "ilu_mg_destroy", "ilu_mg_level", "ilu_mg_cycle", "ilu_mg_solve", "ilu_mg_rate",
@@ -114,6 +114,7 @@ def lib():
         L.ilu_batch_create.argtypes = [vp, i, P(Opts), P(vp)]
         L.ilu_batch_destroy.argtypes = [vp]
         L.ilu_batch_smooth.argtypes = [vp, vp, vp, i, vp]
+        L.ilu_batch_launches.argtypes = [vp, P(i)]
         L.ilu_server_create.argtypes = [P(ServerOpts), P(vp)]
         L.ilu_server_submit.argtypes = [vp, P(Request), P(ctypes.c_uint64)]
         L.ilu_server_wait.argtypes = [vp, ctypes.c_uint64, i, P(Result)]
@@ -468,6 +469,12 @@ class Batch(_Handle):
         xa = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in xs])
         ba = (ctypes.c_void_p * n)(*[None if v is None else _ptr(v).value for v in bs])
         _check(lib().ilu_batch_smooth(self.h, xa, ba, int(sweeps), _stream(stream)))
+
+    def launches_per_sweep(self):
+        """How many kernels one sweep of the batch launches."""
+        n = ctypes.c_int(0)
+        _check(lib().ilu_batch_launches(self.h, ctypes.byref(n)))
+        return n.value
 
 
 class Server(_Handle):

@@ -7,10 +7,14 @@
 //      kernels run concurrently:
 //      - tets whose handles use the packed kernels: one launch per row-table
 //        layout and schedule quantum (level 7 and level 8 schedules differ),
-//        a CTA per tet holding its forward and backward substitution,
-//        tets ordered by their step count, longest first (the CTAs of the
-//        longest tets start first, the short ones fill in behind them); no
-//        CTA waits on another;
+//        a CTA (level 8: a cluster of two) per tet holding its forward and
+//        backward substitution, tets ordered by their step count, longest
+//        first; no CTA waits on another.  The launches follow one another
+//        on the pass's stream, the group with the longest tets first, each
+//        later one a programmatic dependent of the one before: its CTAs are
+//        dispatched once every CTA of the longer group has started, so the
+//        short tets fill the SMs the long ones leave free and never hold an
+//        SM that a long tet's cluster waits for;
 //      - the other tets, grouped by level and row-polynomial layout: one
 //        forward and one backward slab launch per group.  Inside a group the
 //        clusters of every tet take tickets tet by tet, in dependency order
@@ -71,15 +75,14 @@ struct Group {
 };
 
 // Tets on the packed kernels with the same row-table layout and schedule
-// quantum: one launch, a CTA per tet, longest tets first (their CTAs start
-// first).
+// quantum: one launch, a CTA (or cluster) per tet, longest tets first (their
+// CTAs start first).
 struct PackedGroup {
-  int dxp = 0, reg = 0, q = 1, cl = 1;
+  int N = 0, dxp = 0, reg = 0, q = 1, cl = 1;
   bool v1 = false;
   std::vector<int> members;  // tet indices, most steps first
   PackedLaunch pl = {};
-  cudaStream_t st = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;  // after the launch: joins it to the update
 };
 
 }  // namespace
@@ -127,10 +130,8 @@ void free_plan(ilu_batch b) {
     if (g.done) cudaEventDestroy(g.done);
   }
   b->groups.clear();
-  for (auto &g : b->pgroups) {
-    if (g.st) cudaStreamDestroy(g.st);
+  for (auto &g : b->pgroups)
     if (g.done) cudaEventDestroy(g.done);
-  }
   b->pgroups.clear();
   cudaFree(b->d_porder);
   b->d_porder = nullptr;
@@ -199,6 +200,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     const TetView &v = b->views[i];
     if (v.packed) {
       PackedGroup &pg = b->pgroups[pkey[std::make_pair(v.rstride, v.packed_q)]];
+      pg.N = std::max(pg.N, v.N);
       pg.dxp = v.rstride;
       pg.q = v.packed_q;
       pg.cl = v.packed_cl;
@@ -224,6 +226,9 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     std::stable_sort(pg.members.begin(), pg.members.end(),
                      [&](int a, int c) { return b->views[a].packed_steps > b->views[c].packed_steps; });
   }
+  // the group with the largest level (the longest tets) launches first
+  std::stable_sort(b->pgroups.begin(), b->pgroups.end(),
+                   [](const PackedGroup &a, const PackedGroup &c) { return a.N > c.N; });
   int off = 0;
   for (auto &g : b->groups) {
     for (int i : g.members) {
@@ -339,6 +344,7 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     size_t at = 0;
     for (auto &pg : b->pgroups) {
       PackedLaunch &L = pg.pl;
+      L.after_packed = &pg != &b->pgroups.front();
       L.tets = b->d_tets;
       L.order = b->d_porder + at;
       L.ntets = (int)pg.members.size();
@@ -347,7 +353,6 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
       L.cl = pg.cl;
       L.v1 = pg.v1;
       at += pg.members.size();
-      BK(cudaStreamCreateWithFlags(&pg.st, cudaStreamNonBlocking), "cudaStreamCreate");
       BK(cudaEventCreateWithFlags(&pg.done, cudaEventDisableTiming), "cudaEventCreate");
     }
   }
@@ -377,11 +382,12 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
          "batched residual launch");
     }
     BK(cudaEventRecord(b->fork, s), "fork");
-    for (auto &g : b->pgroups) {  // first: the packed launches hold the longest tets
-      BK(cudaStreamWaitEvent(g.st, b->fork, 0), "fork wait");
-      BK(launch_packed(g.pl, g.st), "packed substitution launch");
-      BK(cudaEventRecord(g.done, g.st), "join");
-      BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
+    // the packed groups on this stream, longest tets first, each later launch
+    // a programmatic dependent of the one before; each launch's event joins
+    // it to the update below, whatever the order in which they end
+    for (auto &g : b->pgroups) {
+      BK(launch_packed(g.pl, s), "packed substitution launch");
+      BK(cudaEventRecord(g.done, s), "packed group end");
     }
     for (auto &g : b->groups) {
       BK(cudaStreamWaitEvent(g.st, b->fork, 0), "fork wait");
@@ -390,6 +396,7 @@ ilu_status record_passes(ilu_batch b, int sweeps) {
       BK(cudaEventRecord(g.done, g.st), "join");
       BK(cudaStreamWaitEvent(s, g.done, 0), "join wait");
     }
+    for (auto &g : b->pgroups) BK(cudaStreamWaitEvent(s, g.done, 0), "packed join");
     if (!b->pgroups.empty())  // x += the packed tets' results (the slab tets updated x themselves)
       BK(launch_packed_io(0, b->kind == kSweepMixed, b->d_tets, b->d_iomap, b->total_blocks, b->d_ptrs,
                           nullptr, s),
@@ -541,6 +548,15 @@ ilu_status ilu_batch_destroy(ilu_batch b) {
   ilu::DeviceRestore keep_device;
   if (!b) return ILU_OK;
   release(b);
+  return ILU_OK;
+}
+
+ilu_status ilu_batch_launches(ilu_batch b, int *per_sweep) {
+  if (!b || !per_sweep) return fail(ILU_EINVAL, "null argument");
+  int n = 0;
+  for (int op = 0; op < 3; ++op) n += b->rblocks[op] > 0;  // the residual, one launch per stencil form
+  n += (int)b->pgroups.size() + 2 * (int)b->groups.size() + (b->pgroups.empty() ? 0 : 1);
+  *per_sweep = n;
   return ILU_OK;
 }
 

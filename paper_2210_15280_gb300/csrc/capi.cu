@@ -432,10 +432,11 @@ ilu_status upload(ilu_tet t) {
     ilu_status bs = upload_band(t, t->requested_slabs);
     if (bs != ILU_OK) return bs;
   }
-  // packed kernels: one CTA per tet (see packed.h); measured faster than the
-  // slab kernels for a single tet up to level 6 (F32 sweeps at L5/L6/L7/L8:
-  // 0.086/0.21/1.08/7.98 ms packed, 0.14/0.30/0.63/1.73 ms slab), and the
-  // batch kernel of choice (a CTA per tet, no waits between CTAs)
+  // packed kernels: one CTA (level 8: a cluster of two) per tet (see
+  // packed.h); measured faster than the slab kernels for a single tet up to
+  // level 6 (F32 sweeps at L5/L6/L7/L8: 0.086/0.21/0.70/4.87 ms packed,
+  // 0.14/0.30/0.63/1.73 ms slab), and the batch kernel of choice (no waits
+  // between tets)
   t->use_packed = !t->use_band && t->precision != ILU_F64 && h.dx <= kPackedMaxDegree &&
                   h.L <= kPackedMaxLevel &&
                   (t->kernel_choice == ILU_KERNEL_PACKED || (t->kernel_choice == ILU_KERNEL_AUTO && h.L <= 6));

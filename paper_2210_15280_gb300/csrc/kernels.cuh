@@ -203,11 +203,11 @@ cudaError_t launch_band_in(int kind, int mode, const DevTet *tets, const int *tp
 cudaError_t launch_band_update(int kind, const DevTet *tets, const int *tprefix, int ntets, int total_tiles,
                                void *const *xs, void *x1, cudaStream_t st);
 
-// ---- packed substitutions (packed.cu): one CTA per tet runs its forward and
-// backward substitution on the tet's packed array (which holds r on entry and
+// ---- packed substitutions (packed.cu): one CTA per tet (level 8: a cluster
+// of two) runs its forward and backward substitution on the tet's packed array (which holds r on entry and
 // the backward result on exit).  reg: the degree of the packed row tables (3
 // or 6); v1: some tet uses boundary variant V1.  order (device, nullable): the
-// tet of each CTA.
+// tet of each CTA (cluster).
 struct PackedLaunch {
   const DevTet *tets;
   const int *order;
@@ -216,6 +216,11 @@ struct PackedLaunch {
   int q;    // the schedules' start quantum (1, 2 or 4; the same for every tet of the launch)
   int cl;   // CTAs per tet (1 or 2; the same for every tet of the launch)
   bool v1;
+  // launched as a programmatic dependent of the stream's previous kernel
+  // (itself a packed launch): its CTAs are dispatched once every CTA of that
+  // launch has started, and never wait for its results.  The caller joins
+  // both launches to whatever follows them with events.
+  bool after_packed;
 };
 size_t packed_smem_bytes(int reg);
 cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st);

@@ -430,6 +430,10 @@ template <int DX, bool V1, int Q, int CL>
 __global__ void __launch_bounds__(kPackedLanes, 1) packed_kernel(const DevTet *__restrict__ tets,
                                                                  const int *__restrict__ order) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // a packed launch that follows this one as its programmatic dependent (a
+  // batch's next group) may be dispatched as soon as every CTA of this one
+  // has started: this launch's CTAs take their SMs first
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int b = (int)blockIdx.x / CL;
   const int ti = order ? order[b] : b;
   const DevTet &t = tets[ti];
@@ -442,24 +446,33 @@ cudaError_t launch_one(const PackedLaunch &L, size_t smem, cudaStream_t st) {
   auto k = packed_kernel<DX, V1, Q, CL>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if constexpr (CL == 1) {
+  if (CL == 1 && !L.after_packed) {
     k<<<L.ntets, kPackedLanes, smem, st>>>(L.tets, L.order);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(L.ntets * CL);
-    cfg.blockDim = dim3(kPackedLanes);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k, L.tets, L.order);
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.ntets * CL);
+  cfg.blockDim = dim3(kPackedLanes);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (CL > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (L.after_packed) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  e = cudaLaunchKernelEx(&cfg, k, L.tets, L.order);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -160,3 +160,31 @@ def test_f64_batch_mixing_tabulated_and_evaluated_tets(g):
     batch.close()
     for *_, t in tets:
         t.close()
+
+
+@pytest.mark.parametrize("prec", ["F32", "MIXED"])
+def test_batch_of_packed_tets_with_level8_clusters_equals_single_sweeps(g, prec):
+    """Packed tets of levels 5 to 8 in one batch: the level-8 tets run on
+    clusters of two CTAs, the others on one CTA each (groups by start
+    quantum); every tet's sweeps equal its own handle's bit for bit."""
+    levels, degs = [8, 7, 5, 8, 6], [6, 4, 3, 2, 5]
+    mesh = si.macro_mesh(12, n_tets=len(levels))
+    tp = getattr(g, prec)
+    dtype = torch.float32 if prec == "F32" else torch.float64
+    tets = []
+    for i, (P, L, d) in enumerate(zip(mesh, levels, degs)):
+        co = COEFFS[i % 3]
+        tets.append((P, L, d, co, g.Tet(P, L, coeff=g.make_coeff(*co), poly_degree=d, precision=tp,
+                                        kernel=g.KERNEL_PACKED)))
+    xs, bs = vectors(tets, dtype, 700)
+    ref = [x.clone() for x in xs]
+    for (P, L, d, co, t), x, b in zip(tets, ref, bs):
+        t.smooth(x, b, 2)
+    batch = g.Batch([t for *_, t in tets])
+    batch.smooth(xs, bs, 2)
+    for i, (x, r) in enumerate(zip(xs, ref)):
+        assert torch.isfinite(x).all()
+        assert torch.equal(x, r), f"tet {i} (level {levels[i]}, degree {degs[i]})"
+    batch.close()
+    for *_, t in tets:
+        t.close()

@@ -161,20 +161,19 @@ def level9_sample_points(N, seed, n_random=240):
     return sorted(p for p in pts if p[0] >= 1 and p[1] >= 1 and p[2] >= 1 and sum(p) <= N - 1)
 
 
-@pytest.mark.parametrize("prec,kernel,tol", [("MIXED", "BAND", 1e-5), ("F32", "BAND", 1e-5), ("MIXED", "SLAB", 1e-5),
-                                             ("F64", "AUTO", 1e-12)])
-def test_level9_sweep_solves_the_oracle_residual_equation(g, orc, prec, kernel, tol):
-    """Level 9, the bench's single-tet size, element by element at sampled
-    points: one sweep from x0 (Dirichlet data, interior 0) gives w = x1 - x0
-    = C~^-1 r.  At each sampled point the oracle evaluates the library's
-    exported surrogate polynomials (direct tensor evaluation) on the point's
-    neighbourhood and forms (L~ D~ L~^T w)_p, and computes r_p from its own
-    element-assembled stencil; the two agree to the precision's bar."""
-    level, deg = 9, 6
-    P = si.macro_tet(5)
+def sampled_sweep_check(g, orc, level, prec, kernel, tol, kind="const", deg=6, seed=5):
+    """One sweep from x0 (Dirichlet data, interior 0) gives w = x1 - x0 =
+    C~^-1 r.  At each sampled interior point the oracle evaluates the
+    library's exported surrogate polynomials (direct tensor evaluation) on
+    the point's neighbourhood and forms (L~ D~ L~^T w)_p, and computes r_p
+    from its own element-assembled stencil; the two agree to `tol` relative
+    to the largest |r_p|."""
+    co = {"const": ("const", 1.0, 0.0, 0), "sinprod": ("sinprod", 1.0, 0.5, 0),
+          "kappa_i": ("kappa_i", 0.0, 0.0, 2)}[kind]
+    P = si.macro_tet(seed)
     p = getattr(g, prec)
     dt = torch.float32 if p == g.F32 else torch.float64
-    t = g.Tet(P, level, coeff=g.make_coeff("const"), poly_degree=deg, precision=p,
+    t = g.Tet(P, level, coeff=g.make_coeff(*co), poly_degree=deg, precision=p,
               kernel=getattr(g, "KERNEL_" + kernel))
     N = t.N
     coefs = t.export_surrogate().reshape(8, -1)
@@ -187,16 +186,55 @@ def test_level9_sweep_solves_the_oracle_residual_equation(g, orc, prec, kernel, 
     t.smooth(x, dev(b, dt), 1)
     w = x.cpu().numpy().astype(np.float64) - x0
     del x
+    t.close()
     at = lambda v: (lambda q: v[orc.index(N, *q)])
-    co = orc.Coeff("const")
+    oc = orc.Coeff(*co)
     cache = {}
     lhs, rhs = [], []
     for q in level9_sample_points(N, 13):
         lhs.append(orc.ldlt_apply_at(N, [deg] * 3, coefs, at(w), q, cache))
-        rhs.append(orc.local_residual(P, N, co, at(x0), at(b), q))
+        rhs.append(orc.local_residual(P, N, oc, at(x0), at(b), q))
     lhs, rhs = np.array(lhs), np.array(rhs)
     assert len(rhs) > 250
     assert np.abs(lhs - rhs).max() <= tol * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("prec,kernel,tol", [("MIXED", "BAND", 1e-5), ("F32", "BAND", 1e-5), ("MIXED", "SLAB", 1e-5),
+                                             ("F64", "AUTO", 1e-12)])
+def test_level9_sweep_solves_the_oracle_residual_equation(g, orc, prec, kernel, tol):
+    """Level 9, the bench's single-tet size, element by element at sampled
+    points (sampled_sweep_check)."""
+    sampled_sweep_check(g, orc, 9, prec, kernel, tol)
+
+
+@pytest.mark.parametrize("prec,kind", [("MIXED", "sinprod"), ("F32", "kappa_i"), ("F32", "const")])
+def test_level8_packed_cluster_sweep_solves_the_oracle_residual_equation(g, orc, prec, kind):
+    """Level 8, where the packed kernels run each tet on a cluster of two
+    CTAs (rows of both CTAs read each other's rings), checked against the
+    oracle at sampled points (sampled_sweep_check)."""
+    sampled_sweep_check(g, orc, 8, prec, "PACKED", 1e-5, kind=kind, seed=7)
+
+
+@pytest.mark.parametrize("boundary", ["V2", "V1"])
+def test_level8_packed_cluster_sweeps_equal_slab_sweeps(g, boundary):
+    """Level 8 on the whole grid: three MIXED sweeps of the two-CTA packed
+    kernels land within 1e-5 of the slab kernels' sweeps (whose oracle parity
+    is checked element by element at levels 2 to 7), for both boundary
+    variants."""
+    level, deg = 8, 5
+    P = si.macro_tet(17)
+    co = g.make_coeff("sinprod", 1.0, 0.5, 0)
+    bnd = getattr(g, "BOUNDARY_" + boundary)
+    x0 = si.boundary_data(level, 18)
+    b = dev(si.rhs(level, 19), torch.float64)
+    outs = []
+    for kernel in (g.KERNEL_PACKED, g.KERNEL_SLAB):
+        with g.Tet(P, level, coeff=co, poly_degree=deg, precision=g.MIXED, kernel=kernel, boundary=bnd) as t:
+            x = dev(x0, torch.float64)
+            t.smooth(x, b, 3)
+            outs.append(x.cpu().numpy())
+    assert np.isfinite(outs[0]).all()
+    assert rel(outs[0], outs[1]) < 1e-5
 
 
 @pytest.mark.parametrize("prec", ["F64", "MIXED", "F32"])

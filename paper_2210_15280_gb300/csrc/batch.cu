@@ -265,8 +265,10 @@ ilu_status build(ilu_batch b, int zb_pref, bool largest) {
     for (int op = 0; op < 3; ++op) {
       b->rat[op] = rmap.size();
       for (int i = 0; i < n; ++i)
-        if (residual_op(b->dev[i]) == op)
-          for (int k = 0; k < residual_blocks(b->views[i].N); ++k) rmap.push_back(make_int2(i, k));
+        if (residual_op(b->dev[i]) == op) {
+          const int nb = op == kOpConst ? residual_strip_blocks(b->views[i].N) : residual_blocks(b->views[i].N);
+          for (int k = 0; k < nb; ++k) rmap.push_back(make_int2(i, k));
+        }
       b->rblocks[op] = (int)(rmap.size() - b->rat[op]);
     }
     BK(cudaMalloc(&b->d_rmap, sizeof(int2) * std::max<size_t>(rmap.size(), 1)), "cudaMalloc residual maps");

@@ -84,6 +84,7 @@ struct ilu_tet_s {
   const int *band_tprefix = nullptr;
   int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
   int *d_chunks = nullptr;  // residual work list (32-point row chunks)
+  int *d_strips = nullptr;  // constant-stencil residual work list (strips)
   WaveLaunch wl = {};       // the forward/backward launch shape of this tet
   LaunchStatus *d_status = nullptr, *h_status = nullptr;
   int nblocks = 0, norms_cap = 0;
@@ -132,8 +133,8 @@ void free_device(ilu_tet t) {
   t->d_bnd = nullptr;
   t->d_bnd_off = nullptr;
   cudaFree(t->d_partials); cudaFree(t->d_norms); cudaFree(t->d_flags); cudaFree(t->d_status);
-  cudaFree(t->d_dev); cudaFree(t->d_map); cudaFree(t->d_chunks);
-  t->d_dev = nullptr; t->d_map = nullptr; t->d_chunks = nullptr;
+  cudaFree(t->d_dev); cudaFree(t->d_map); cudaFree(t->d_chunks); cudaFree(t->d_strips);
+  t->d_dev = nullptr; t->d_map = nullptr; t->d_chunks = nullptr; t->d_strips = nullptr;
   cudaFree(t->d_binfo); cudaFree(t->d_bint); cudaFree(t->d_bw); cudaFree(t->d_bstreams);
   t->d_binfo = nullptr; t->d_bint = nullptr; t->d_bw = nullptr; t->d_bstreams = nullptr;
   cudaFree(t->d_xs); cudaFree(t->d_bs);
@@ -422,6 +423,14 @@ ilu_status upload(ilu_tet t) {
          "upload residual chunks");
     t->dev.chunks = t->d_chunks;
     t->dev.nchunks = (int)chunks.size();
+    std::vector<int> strips(residual_strips(h.N));
+    residual_strip_list(h.N, strips.data());
+    CK(cudaMalloc(&t->d_strips, sizeof(int) * std::max<size_t>(strips.size(), 1)), "cudaMalloc residual strips");
+    if (!strips.empty())
+      CK(cudaMemcpy(t->d_strips, strips.data(), sizeof(int) * strips.size(), cudaMemcpyHostToDevice),
+         "upload residual strips");
+    t->dev.strips = t->d_strips;
+    t->dev.nstrips = (int)strips.size();
   }
   CK(cudaMalloc(&t->d_dev, sizeof(DevTet)), "cudaMalloc tet");
   // band kernels: measured faster than the slab kernels from level 9 on

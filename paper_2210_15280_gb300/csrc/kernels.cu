@@ -109,10 +109,116 @@ __device__ __forceinline__ double residual_chunk(const StencilData &t, const TR 
   return (double)res * (double)res;
 }
 
+// ---- constant stencil: strips.  A warp takes the points (x0 .. x0 + 29, y,
+// z) of up to kStripRows consecutive rows y = y0, y0 + 1, ...  Lane l holds
+// grid point x0 - 1 + l of every row it loads: lanes 1..30 own the strip's
+// points and lanes 0 and 31 only lend their values to the neighbours, which
+// take x - 1 and x + 1 from the adjacent lanes.  A point's stencil touches
+// the rows (y-1, z) (y, z) (y+1, z) of its layer, (y, z-1) (y+1, z-1) below
+// and (y-1, z+1) (y, z+1) above; one row further on, four of them are kept
+// and three are loaded (one step ahead, with the next step's b).  The sum
+// runs over the directions in the order of the chunk form, so both give the
+// same bits.
+template <typename TR>
+struct StripRow {
+  TR m, c, p;  // the row at x - 1, x, x + 1
+};
+template <typename TR>
+__device__ __forceinline__ StripRow<TR> strip_row(TR c) {
+  StripRow<TR> r;
+  r.c = c;
+  r.m = __shfl_up_sync(0xffffffffu, c, 1);
+  r.p = __shfl_down_sync(0xffffffffu, c, 1);
+  return r;
+}
+// U: rows unrolled (kStripRows: the rows rotate through registers without
+// copies; fewer where the registers do not hold them)
+template <typename TX, typename TR, typename TW, int U = kStripRows>
+__device__ __forceinline__ double residual_strip(const TR *A15, int N, int strip, int lane,
+                                                 const TX *__restrict__ x, const TX *__restrict__ b,
+                                                 TW *__restrict__ r, const int *__restrict__ pmap,
+                                                 float *__restrict__ pw, int plane) {
+  const int x0 = strip & 1023, y0 = (strip >> 10) & 1023, z = strip >> 20;
+  const int xl = x0 - 1 + lane;
+  const int ny = min(kStripRows, N - z - x0 - y0);  // rows holding a point: x0 + y + z <= N - 1
+  // A lane past the end of a row reads a point of a later row instead (the
+  // index clamped to the grid's last point): only lanes that own no point of
+  // the strip use such a value, so every load is unconditional.
+  const int last = (N + 1) * (N + 2) * (N + 3) / 6 - 1;
+  auto ld = [&](int i) -> TR { return (TR)x[min(i, last)]; };
+  // row y' of layer z' holds x = 0 .. K - y' (K = N - z'): K - y' + 1 points
+  const int Kz = N - z, Kb = N - z + 1, Kt = N - z - 1;
+  // lane's grid index in the row each layer loads next
+  int sz = row_start32(N, y0 - 1, z) + xl, sb = row_start32(N, y0, z - 1) + xl,
+      st = row_start32(N, y0 - 1, z + 1) + xl;
+  StripRow<TR> zm = strip_row(ld(sz));  // (y0 - 1, z)
+  sz += Kz - y0 + 2;
+  StripRow<TR> zc = strip_row(ld(sz));  // (y0, z)
+  sz += Kz - y0 + 1;
+  StripRow<TR> bc = strip_row(ld(sb));  // (y0, z - 1)
+  sb += Kb - y0 + 1;
+  StripRow<TR> tm = strip_row(ld(st));  // (y0 - 1, z + 1)
+  st += Kt - y0 + 2;
+  int rc = row_start32(N, y0, z) + xl;
+  const int *pm = pmap ? pmap + row_id32(N, y0, z) : nullptr;  // row ids of a layer are consecutive in y
+  // the first step's new rows (y0 + 1, z), (y0 + 1, z - 1), (y0, z + 1), its b and packed row
+  TR nz = ld(sz), nb = ld(sb), nt = ld(st), nbv = (TR)b[min(rc, last)];
+  int npm = pm ? pm[0] : 0;
+  double acc2 = 0.0;
+#pragma unroll U
+  for (int j = 0; j < kStripRows; ++j) {
+    if (j >= ny) break;
+    const int y = y0 + j;
+    const StripRow<TR> zp = strip_row(nz), bp = strip_row(nb), tc = strip_row(nt);
+    TR res = nbv;
+    const int pmv = npm, rcy = rc;
+    // the next step's loads: rows (y + 2, z), (y + 2, z - 1), (y + 1, z + 1)
+    sz += Kz - y;
+    sb += Kb - y;
+    st += Kt - y + 1;
+    rc += Kz - y + 1;
+    nz = ld(sz);
+    nb = ld(sb);
+    nt = ld(st);
+    nbv = (TR)b[min(rc, last)];
+    if (pm && j + 1 < ny) npm = pm[j + 1];
+    // w s se bnw bn bc be c e n nw tse ts tc tw
+    res = fma(-A15[0], zc.m, res);
+    res = fma(-A15[1], zm.c, res);
+    res = fma(-A15[2], zm.p, res);
+    res = fma(-A15[3], bp.m, res);
+    res = fma(-A15[4], bp.c, res);
+    res = fma(-A15[5], bc.c, res);
+    res = fma(-A15[6], bc.p, res);
+    res = fma(-A15[7], zc.c, res);
+    res = fma(-A15[8], zc.p, res);
+    res = fma(-A15[9], zp.c, res);
+    res = fma(-A15[10], zp.m, res);
+    res = fma(-A15[11], tm.p, res);
+    res = fma(-A15[12], tm.c, res);
+    res = fma(-A15[13], tc.c, res);
+    res = fma(-A15[14], tc.m, res);
+    if (lane >= 1 && lane <= kStripWidth && xl <= N - 1 - y - z) {
+      if (pmap)
+        pw[packed_index32((pmv & 0xfffff) + xl - 1, pmv >> 20, plane)] = (float)res;
+      else
+        r[rcy] = (TW)res;
+      acc2 += (double)res * (double)res;
+    }
+    zm = zc;
+    zc = zp;
+    bc = bp;
+    tm = tc;
+  }
+  return acc2;
+}
+
 // CTAs per SM the residual launches are compiled for (their register budget)
-template <int MODE>
+// (strips hold seven rows of three values, and the single-tet kernel its
+// norm as well: three CTAs, 80 registers, except for the FP32 batch form)
+template <int MODE, typename TR, bool BATCH>
 constexpr int residual_min_blocks() {
-  return MODE == kOpStar ? 2 : 4;
+  return MODE == kOpStar ? 2 : (MODE == kOpConst && (sizeof(TR) == 8 || !BATCH) ? 3 : 4);
 }
 
 // The constant stencil of a block in the residual type: FP32 coefficients
@@ -137,7 +243,7 @@ struct ConstStencil {
 // warps in all; the launch sizes the grid to the CTAs the GPU holds at once,
 // so no partial last wave), per-block partial norms.
 template <typename TX, typename TR, typename TW, int MODE>
-__global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_kernel(
+__global__ void __launch_bounds__(256, residual_min_blocks<MODE, TR, false>()) residual_kernel(
     DevTet t, const TX *__restrict__ x, const TX *__restrict__ b, TW *__restrict__ r, double *__restrict__ partials,
     bool packed) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,10 +252,18 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_ker
   const TR *A15 = cs.load(t.A15, sA15);
   const StencilData sd{t.Wstar, t.kappa, t.astore, t.astride, t.pk.lanes};
   double acc2 = 0.0;
+  if constexpr (MODE == kOpConst) {
 #pragma unroll 1
-  for (int c = blockIdx.x * 8 + warp; c < t.nchunks; c += gridDim.x * 8)  // warp-uniform
-    acc2 += residual_chunk<TX, TR, TW, MODE>(sd, A15, t.N, t.chunks[c], lane, x, b, r,
-                                             packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
+    for (int c = blockIdx.x * 8 + warp; c < t.nstrips; c += gridDim.x * 8)  // warp-uniform
+      acc2 += residual_strip<TX, TR, TW, sizeof(TR) == 4 ? 4 : 2>(
+          A15, t.N, t.strips[c], lane, x, b, r, packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr,
+          t.pk.lanes);
+  } else {
+#pragma unroll 1
+    for (int c = blockIdx.x * 8 + warp; c < t.nchunks; c += gridDim.x * 8)  // warp-uniform
+      acc2 += residual_chunk<TX, TR, TW, MODE>(sd, A15, t.N, t.chunks[c], lane, x, b, r,
+                                               packed ? t.pk.row_map : nullptr, packed ? t.pk.pw : nullptr);
+  }
   // deterministic block reduction of the squared norm
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
@@ -169,7 +283,7 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>()) residual_ker
 // its scratch w.  One launch per operator kind keeps the register count of
 // each kernel that of its own arithmetic.
 template <typename TX, typename TR, typename TW, int MODE>
-__global__ void __launch_bounds__(256, residual_min_blocks<MODE>())
+__global__ void __launch_bounds__(256, residual_min_blocks<MODE, TR, true>())
     residual_batch_kernel(const DevTet *__restrict__ tets, const int2 *__restrict__ bmap,
                           const TX *const *__restrict__ xs, const TX *const *__restrict__ bs) {
   const int2 bm = bmap[blockIdx.x];
@@ -187,6 +301,11 @@ __global__ void __launch_bounds__(256, residual_min_blocks<MODE>())
   const int *pmap = tg.pk.pw ? tg.pk.row_map : nullptr;
   float *pw = tg.pk.pw;
   const TX *xv = xs[bm.x], *bv = bs[bm.x];
+  if constexpr (MODE == kOpConst) {  // a strip per warp (no block-wide synchronisation follows)
+    const int si = bm.y * 8 + warp;
+    if (si < tg.nstrips) residual_strip<TX, TR, TW>(A15, N, tg.strips[si], lane, xv, bv, r, pmap, pw, tg.pk.lanes);
+    return;
+  }
 #pragma unroll 1
   for (int k = 0; k < kResidualCPW && c0 + k < nch; ++k)  // no block-wide synchronisation follows
     residual_chunk<TX, TR, TW, MODE>(sd, A15, N, chunks[c0 + k], lane, xv, bv, r, pmap, pw);
@@ -299,19 +418,37 @@ void residual_chunk_list(int N, int *out) {
       for (int x = 1; x <= N - 1 - y - z; ++x, ++k)
         if (k % 32 == 0) out[i++] = x | y << 10 | z << 20;
 }
+// strips: layer z has interior points with x <= N - 2 - z (at y = 1), and
+// the strip at x0 rows y with x0 + y + z <= N - 1
+template <typename F>
+static void for_each_strip(int N, F f) {
+  for (int z = 1; z <= N - 3; ++z)
+    for (int x0 = 1; x0 <= N - 2 - z; x0 += kStripWidth)
+      for (int y0 = 1; x0 + y0 + z <= N - 1; y0 += kStripRows) f(x0 | y0 << 10 | z << 20);
+}
+int residual_strips(int N) {
+  int n = 0;
+  for_each_strip(N, [&](int) { ++n; });
+  return n;
+}
+void residual_strip_list(int N, int *out) {
+  int i = 0;
+  for_each_strip(N, [&](int s) { out[i++] = s; });
+}
+int residual_strip_blocks(int N) { return (residual_strips(N) + 7) / 8; }
 
 cudaError_t launch_residual(const DevTet &t, int kind, const void *x, const void *b, void *r_out, double *partials,
                             int nblocks_cap, int *nblocks_used, cudaStream_t st, bool packed) {
   if (packed && (!t.pk.pw || kind == kSweepF64)) return cudaErrorInvalidValue;
-  if (!t.chunks || nblocks_cap < 1) return cudaErrorInvalidValue;
-  const int want = (t.nchunks + 7) / 8;  // a warp per chunk
+  if (!t.chunks || !t.strips || nblocks_cap < 1) return cudaErrorInvalidValue;
+  const int mode = t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar);
+  const int want = ((mode == kOpConst ? t.nstrips : t.nchunks) + 7) / 8;  // a warp per strip or chunk
   if (nblocks_used) *nblocks_used = 0;
   if (want == 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int mode = t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar);
   auto go = [&](auto tx, auto tr, auto tw, auto m) {
     using TX = decltype(tx);
     using TR = decltype(tr);

@@ -72,6 +72,9 @@ struct DevTet {
   const int *chunks; // residual work list: first point x | y << 10 | z << 20 of each run of 32
                      // interior points in lexicographic order (chunk_point in grid.h)
   int nchunks;
+  const int *strips; // constant-stencil residual work list: x0 | y0 << 10 | z << 20 of each strip
+                     // (residual_strip_list)
+  int nstrips;
   const void *astore;    // variable kappa, stored operator: coefficient of direction d (d != centre) of
                          // row p at astore[(d < 7 ? d : d - 1) * astride + p], double (float in F32
                          // sweeps); null: assembled on the fly
@@ -107,7 +110,7 @@ constexpr int kOpConst = 0, kOpStar = 1, kOpStored = 2;
 inline int residual_op(const DevTet &t) { return t.const_kappa ? kOpConst : (t.astore ? kOpStored : kOpStar); }
 // Residual of many tets with the same residual_op in one launch: block i of
 // the 1-D grid is block bmap[i].y of tet bmap[i].x (residual_blocks(N) per
-// tet); tets, bmap and the per-tet pointer arrays (indexed by tet) are device
+// tet, residual_strip_blocks(N) for the constant stencil); tets, bmap and the per-tet pointer arrays (indexed by tet) are device
 // memory.  Writes w of each tet, or its packed array if it has one; no norms.
 cudaError_t launch_residual_batch(const DevTet *tets, const int2 *bmap, int total_blocks, int kind, int op,
                                   const void *const *xs, const void *const *bs, cudaStream_t st);
@@ -176,6 +179,13 @@ int residual_blocks(int N);  // blocks of the residual launch (8 warps of kResid
 int rowgrid_blocks(int N);   // blocks of the row-per-warp reductions (interior norm)
 int residual_chunks(int N);
 void residual_chunk_list(int N, int *out);
+// Strips of the constant-stencil residual: a warp takes the interior points
+// (x0 .. x0 + kStripWidth - 1, y, z) of kStripRows consecutive rows y0 ..;
+// z-major, then x0, then y0.
+constexpr int kStripWidth = 30, kStripRows = 16;
+int residual_strips(int N);
+void residual_strip_list(int N, int *out);
+int residual_strip_blocks(int N);  // blocks of 8 warps, a strip per warp
 
 // ---- FP32 band sweeps (band.cu)
 

@@ -238,9 +238,12 @@ def test_level8_packed_cluster_sweeps_equal_slab_sweeps(g, boundary):
 
 
 @pytest.mark.parametrize("prec", ["F64", "MIXED", "F32"])
-def test_residual_matches_oracle(g, orc, prec):
-    level = 5
-    P, co, pr = problem(orc, level, 71, "sinprod", 3)
+@pytest.mark.parametrize("level,kind", [(5, "sinprod"), (5, "const"), (6, "const"), (3, "const")])
+def test_residual_matches_oracle(g, orc, prec, level, kind):
+    """r = b - A x element by element: variable kappa (chunk form) and the
+    constant stencil (strips of 30 points x 16 rows, several per layer at
+    level 6, ragged at the layers' edges)."""
+    P, co, pr = problem(orc, level, 71, kind, 3)
     N = 2 ** level
     p = getattr(g, prec)
     t = gpu_tet(g, P, level, co, 3, p, pr.coefs)

@@ -314,23 +314,22 @@ ilu_status ilu_solve(ilu_tet t, void *x, const void *b, int method, double rtol,
 /* The row schedule the packed kernels (ILU_KERNEL_PACKED) follow for one
  * substitution at a level (the same for every tet of that level), for
  * inspection and testing.  lanes: 0 for the kernels' own lane count (384 up
- * to level 7, 768 -- two CTAs -- at level 8), else 1..1023 for the
+ * to level 7, 640 -- two CTAs of 320 -- at level 8), else 1..1016 for the
  * same construction on that many lanes; quantum: 0 for the
  * kernels' start quantum at that level (1 up to level 6, 2 at 7, 4 at 8),
  * else 1, 2 or 4.  *nsteps and *lanes_out receive its size; with entries and
  * lane_off (lanes + 1 ints) non-null they receive the schedule, rows grouped
  * by lane in step order, 8 ints per interior row, in the pass's own steps:
- *   [0] sw | (lo - sw) << 16: the row's switch step sw (quantum - 1 modulo
- *       the quantum; the lane computes no point there) and the step lo of
- *       its first point;
+ *   [0] sw | (lo - sw) << 16 | far << 20: the row's switch step sw
+ *       (quantum - 1 modulo the quantum; the lane computes no point there),
+ *       the step lo of its first point, and bit j of far set if producer j
+ *       is read from global memory;
  *   [1] n | y << 10 | z << 20, n the row's point count;
- *   [2] R0 | R1 << 14 | far << 28 and [3] R2 | row id << 14 | cta << 29:
- *       R_j the word of a CTA's shared ring (384 + 8 words a step) holding
- *       producer j's value read at the first step of the 8-step block holding
- *       sw (word 384, never written, if the producer row does not exist or is
- *       read from global memory), bit j of far set for the latter, bit j of
- *       cta the CTA whose ring it is (lane / 384; the consumer's own CTA for
- *       word 384);
+ *   [2] R0 | R1 << 15 and [3] R2 | row id << 15: R_j the word of the shared
+ *       ring (lanes + 8 words a step; in a cluster every CTA holds all of
+ *       it) holding producer j's value read at the first step of the 8-step
+ *       block holding sw (word `lanes`, never written, if the producer row
+ *       does not exist or is read from global memory);
  *   [4] the row coordinate (2x - (N - y - z)) / (2N) of step sw's point
  *       (float bits; x = 0 forward, n + lo - sw backward);
  *   [5..7] the producer codes: mode in bits 30-31 (0 no such interior row,

@@ -79,7 +79,7 @@ struct ilu_tet_s {
   bool use_packed = false;
   void *d_pkF = nullptr, *d_pkB = nullptr;  // compact row polynomials of the packed kernels
   int4 *d_pk = nullptr;      // schedules, lane offsets and row map in one block
-  float *d_pkw = nullptr;    // the packed array [T][kPackedLanes]
+  float *d_pkw = nullptr;    // the packed array [T][lanes]
   PackedLaunch pl = {};
   const int *band_tprefix = nullptr;
   int *d_map = nullptr;     // cluster prefixes {0, Qf}, {0, Qb} and the order {0}
@@ -382,7 +382,7 @@ ilu_status upload_packed(ilu_tet t) {
   L.ntets = 1;
   L.reg = packed_degree(t->host.dx);
   L.q = pl->q;
-  L.cl = pl->lanes / kPackedLanes;
+  L.cl = pl->lanes > kPackedLanes ? 2 : 1;
   L.v1 = t->host.boundary == ILU_BOUNDARY_V1;
   return ILU_OK;
 }
@@ -1194,14 +1194,14 @@ ilu_status ilu_packed_schedule(int level, int forward, int lanes, int quantum, i
                                int *entries, int *lane_off) {
   if (!nsteps || !lanes_out) return fail(ILU_EINVAL, "null argument");
   if (level < 2 || level > kPackedMaxLevel) return fail(ILU_EINVAL, "the packed schedules cover levels 2 to 8");
-  if (lanes < 0 || lanes > 1023) return fail(ILU_EINVAL, "lanes must be 0 (the kernels' count) or 1..1023");
+  if (lanes < 0 || lanes > 1016) return fail(ILU_EINVAL, "lanes must be 0 (the kernels' count) or 1..1016");
   if (quantum != 0 && quantum != 1 && quantum != 2 && quantum != 4)
     return fail(ILU_EINVAL, "quantum must be 0 (the kernels' own), 1, 2 or 4");
   const int N = 1 << level, q = quantum ? quantum : packed_quantum(N);
   std::string err;
   PackedPlan own;
   const PackedPlan *p = nullptr;
-  const int own_lanes = packed_cluster(N) * kPackedLanes;
+  const int own_lanes = packed_lanes(N);
   if ((lanes == 0 || lanes == own_lanes) && q == packed_quantum(N)) {
     p = packed_plan_cached(N, &err);
   } else if (make_packed_plan(N, lanes ? lanes : own_lanes, q, &own, &err)) {

@@ -39,14 +39,14 @@ struct BandDev {
 // Row schedules of the packed substitutions (packed.h): the PackedEntry
 // records (two int4 each) of either pass grouped by lane, the lane offsets
 // (the same for both), per row id its forward first step | lane << 20, the
-// packed step-major array [nsteps][kPackedLanes] and its step count.
+// packed step-major array [nsteps][lanes] and its step count.
 struct PackedDev {
   const int4 *ent_f, *ent_b;
   const int *off;
   const int *row_map;
   float *pw;
   int nsteps;
-  int lanes;  // lanes of the schedule: kPackedLanes per CTA of the tet's cluster
+  int lanes;  // lanes of the schedule: all lanes of the tet's CTA or cluster
 };
 
 // Everything a kernel needs to know about one tet.  Plain old data so that it
@@ -232,7 +232,7 @@ struct PackedLaunch {
   // both launches to whatever follows them with events.
   bool after_packed;
 };
-size_t packed_smem_bytes(int reg);
+size_t packed_smem_bytes(int reg, int cl);
 cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st);
 // Between a tet's lexicographic vectors and its packed array, over the
 // residual chunk list (block i of the grid is block bmap[i].y of tet

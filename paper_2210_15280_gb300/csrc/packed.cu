@@ -1,14 +1,15 @@
 // packed.cu -- packed substitution kernels of the FP32 sweeps (Alg. 2 of
 // arXiv 2210.15280 with the V2 boundary rule; V1 as an option).
 //
-// One CTA of kPackedLanes threads per macro-tetrahedron runs the forward
-// substitution
+// One CTA of kPackedLanes threads per macro-tetrahedron (at level 8 a
+// cluster of two CTAs of kPackedClusterLanes threads, each holding the
+// whole ring) runs the forward substitution
 //     w^p = r^p - sum_{d in D_l, p+d interior} L~^p_d w^{p+d}
 // and then the backward substitution
 //     w^p <- D~^-1(p) w^p - sum_{d in D_l, p-d interior} L~^{p-d}_d w^{p-d},
 // walking the steps of the tet's host-computed row schedule (packed.h): at
 // step tau every lane computes one point of the row it owns (or writes 0),
-// and every Q steps the CTA meets at a block barrier.  No CTA waits on
+// and every Q steps the CTA (cluster) meets at a barrier.  No tet waits on
 // another.  Everything the
 // passes read and write lies in the tet's step-major packed array, where the
 // lanes of a warp touch consecutive words at every step; packed_io_kernel
@@ -37,9 +38,12 @@
 namespace ilu {
 namespace {
 
-constexpr int LN = kPackedLanes, RG = kPackedRing, QS = kPackedQueue, PD = kPackedPre;
-constexpr int RW = kPackedRingRow;         // words per ring row; column LN is never written (reads 0)
+constexpr int RG = kPackedRing, QS = kPackedQueue, PD = kPackedPre;
 constexpr int RR = RG + kPackedBlock;      // ring rows: RG, then a mirror of rows 0 .. kPackedBlock - 1
+// threads per CTA, and words per ring row (all lanes of the tet's CTA or
+// cluster, then 8 words; column CL * cta_lanes(CL) is never written: reads 0)
+__host__ __device__ constexpr int cta_lanes(int cl) { return cl > 1 ? kPackedClusterLanes : kPackedLanes; }
+__host__ __device__ constexpr int ring_row(int cl) { return packed_ring_row(cl * cta_lanes(cl)); }
 static_assert((RG & (RG - 1)) == 0 && (QS & (QS - 1)) == 0, "ring and queue sizes are powers of two");
 static_assert(QS == kPackedBlock, "a step's queue slot is its index in the unrolled block");
 static_assert(RG % kPackedBlock == 0, "blocks tile the ring");
@@ -77,9 +81,9 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ int pmode(int code) { return (code >> 30) & 3; }
 
 // cluster primitives: this CTA's rank, the cluster-window address of a
-// shared location in CTA `rank`, a load through that window, and a barrier of
-// every thread of the cluster (release / acquire: shared-memory writes before
-// it are visible to every CTA after it)
+// shared location in CTA `rank`, a store through that window, and a barrier
+// of every thread of the cluster (release / acquire: shared-memory writes
+// before it, the other CTA's included, are visible to every CTA after it)
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -90,10 +94,8 @@ __device__ __forceinline__ unsigned cluster_addr(const void *p, unsigned rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
   return a;
 }
-__device__ __forceinline__ float ld_cluster(unsigned a) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
-  return v;
+__device__ __forceinline__ void st_cluster(unsigned a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -144,14 +146,16 @@ __device__ __forceinline__ void pass_sync() {
 template <bool FWD, int DX, bool V1, int Q, int CL>
 __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem) {
   constexpr int SF2 = 4 * (DX + 1);  // float2 of a staged row: coefficient k of the four function pairs
+  constexpr int LN = cta_lanes(CL);  // this CTA's lanes
+  constexpr int LT = CL * LN;        // lanes of the schedule and the packed array
+  constexpr int RW = ring_row(CL);
   float *ring = reinterpret_cast<float *>(smem);                 // [RR][RW]
   float4 *q = reinterpret_cast<float4 *>(ring + RR * RW);        // [QS][LN] far producer values (.y .z .w)
   int4 *sent = reinterpret_cast<int4 *>(q + QS * LN);            // [LN][2]
   float2 *stage = reinterpret_cast<float2 *>(sent + 2 * LN);     // [LN][SF2]
   const int lane = threadIdx.x;                                    // this CTA's lane (stage, sent)
   const unsigned rank = CL > 1 ? cluster_rank() : 0u;
-  const int lg = (int)rank * LN + lane;                            // the schedule's lane
-  const int LT = CL * LN;                                          // lanes of the schedule and the packed array
+  const int lg = (int)rank * LN + lane;                            // the schedule's lane (ring column)
   const int N = t.N;
   const int4 *ent = FWD ? t.pk.ent_f : t.pk.ent_b;  // entry e at ent[2e], ent[2e + 1]
   const int *off = t.pk.off;
@@ -161,7 +165,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   const float hh = (float)(0.5 * t.h);
   float2 *my_stage = stage + lane * SF2;
 
-  // ring rows of steps before 0 read as 0; column LN stays 0 for good
+  // ring rows of steps before 0 read as 0; column LT stays 0 for good
   {
     float4 *r4 = reinterpret_cast<float4 *>(ring);
     for (int i = lane; i < RR * RW / 4; i += LN) r4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -192,8 +196,8 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   // the cursor moves to the next row at step tau2 = its switch step: its far
   // producers, and the copies of its coefficients and of the entry after it
   auto cursor = [&](int tau2) {
-    pgm = (nxa.z >> 28) & 7;
-    const int lo = (nxa.x & 0xffff) + (nxa.x >> 16);
+    pgm = (nxa.x >> 20) & 7;
+    const int lo = (nxa.x & 0xffff) + ((nxa.x >> 16) & 15);
     pf_end = lo + (nxa.y & 1023) - 1;
     auto pos0 = [&](int code) {  // the value read at step tau2
       return packed_index32(ppos(tau2 - ((code >> 10) & 0xfffff) + 1), code & 1023, LT);
@@ -203,7 +207,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
       o1 = pos0(nxb.z);
       o2 = pos0(nxb.w);
     }
-    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)(((unsigned)nxa.w >> 14) & 0x7fffu) * SF2);
+    const float4 *src = reinterpret_cast<const float4 *>(tab + (size_t)(((unsigned)nxa.w >> 15) & 0x7fffu) * SF2);
     float4 *dst = reinterpret_cast<float4 *>(my_stage);
 #pragma unroll
     for (int i = 0; i < SF2 / 2; ++i) cpa16(dst + i, src + i);
@@ -238,11 +242,10 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   // current row
   int lo = 0, cn = 0, c_y = 0, c_z = 0;
   int gm = 0;                       // bit j: producer j comes through the queue
-  int B0 = LN, B1 = LN, B2 = LN;    // ring word of each producer's read at the block's first step
-  // CL > 1: cluster-window base of each producer's ring; until the lane's
-  // first row, its own ring (the reads give the column nothing writes)
-  unsigned A0 = 0, A1 = 0, A2 = 0;
-  if constexpr (CL > 1) A0 = A1 = A2 = cluster_addr(ring, rank);
+  int B0 = LT, B1 = LT, B2 = LT;    // ring word of each producer's read at the block's first step
+  // CL > 1: the other CTA's ring in the cluster window (every result is
+  // stored there too)
+  const unsigned peer = CL > 1 ? cluster_addr(ring, rank ^ 1u) : 0u;
   float cv0 = 0.f, cv1 = 0.f, cv2 = 0.f;  // each producer's value of the last step
   float v1 = 0.f;                         // this lane's value of the last step
   float2 t2 = make_float2(0.f, 0.f);
@@ -255,20 +258,14 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     for (int k = 0; k <= DX; ++k) c[p][k] = make_float2(0.f, 0.f);
 
   auto switch_row = [&]() {  // on the next row's switch step
-    lo = (nxa.x & 0xffff) + (nxa.x >> 16);
+    lo = (nxa.x & 0xffff) + ((nxa.x >> 16) & 15);
     cn = nxa.y & 1023;
     c_y = (nxa.y >> 10) & 1023;
     c_z = nxa.y >> 20;
-    B0 = nxa.z & 0x3fff;
-    B1 = (nxa.z >> 14) & 0x3fff;
-    B2 = nxa.w & 0x3fff;
-    gm = (nxa.z >> 28) & 7;
-    if constexpr (CL > 1) {
-      const unsigned cta = (unsigned)nxa.w >> 29;
-      A0 = cluster_addr(ring, cta & 1);
-      A1 = cluster_addr(ring, (cta >> 1) & 1);
-      A2 = cluster_addr(ring, (cta >> 2) & 1);
-    }
+    B0 = nxa.z & 0x7fff;
+    B1 = (nxa.z >> 15) & 0x7fff;
+    B2 = nxa.w & 0x7fff;
+    gm = (nxa.x >> 20) & 7;
     const float tt = __int_as_float(nxb.x);
     t2 = make_float2(tt, tt);
     const float4 *sv = reinterpret_cast<const float4 *>(my_stage);
@@ -298,16 +295,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     if (((J + PD) & (Q - 1)) == Q - 1 && tau + PD == ev) cursor(tau + PD);
     prefetch(tau + PD);
     // each producer's second value of this step
-    float r0, r1, r2;
-    if constexpr (CL > 1) {
-      r0 = ld_cluster(A0 + 4u * (unsigned)(B0 + J * RW));
-      r1 = ld_cluster(A1 + 4u * (unsigned)(B1 + J * RW));
-      r2 = ld_cluster(A2 + 4u * (unsigned)(B2 + J * RW));
-    } else {
-      r0 = ring[B0 + J * RW];
-      r1 = ring[B1 + J * RW];
-      r2 = ring[B2 + J * RW];
-    }
+    float r0 = ring[B0 + J * RW], r1 = ring[B1 + J * RW], r2 = ring[B2 + J * RW];
     if (gm) {
       const float4 qv = q[J * LN + lane];
       if (gm & 1) r0 = qv.y;
@@ -381,7 +369,11 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
     const float out = active ? acc : 0.f;
     v1 = out;
     ring[wb + J * RW] = out;
-    if (mir) ring[(RG + J) * RW + lane] = out;
+    if (mir) ring[(RG + J) * RW + lg] = out;
+    if constexpr (CL > 1) {  // the same words of the other CTA's ring (visible there after the barrier)
+      st_cluster(peer + 4u * (unsigned)(wb + J * RW), out);
+      if (mir) st_cluster(peer + 4u * (unsigned)((RG + J) * RW + lg), out);
+    }
     if ((J & (Q - 1)) == Q - 1) pass_sync<CL>();  // every Q steps (producers are at least Q + 1 steps ahead)
     return out;
   };
@@ -392,7 +384,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
   for (int g = 0; g < G; ++g) {
     const int tau0 = g * kPackedBlock;
     const bool mir = (g & (RG / kPackedBlock - 1)) == 0;  // ring rows 0..7: also write their mirror
-    const int wb = (tau0 & (RG - 1)) * RW + lane;
+    const int wb = (tau0 & (RG - 1)) * RW + lg;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g4 = 2 * g + h;
@@ -427,7 +419,7 @@ __device__ __forceinline__ void packed_pass(const DevTet &t, unsigned char *smem
 
 // one cluster of CL CTAs per tet (CL consecutive blocks)
 template <int DX, bool V1, int Q, int CL>
-__global__ void __launch_bounds__(kPackedLanes, 1) packed_kernel(const DevTet *__restrict__ tets,
+__global__ void __launch_bounds__(cta_lanes(CL), 1) packed_kernel(const DevTet *__restrict__ tets,
                                                                  const int *__restrict__ order) {
   extern __shared__ __align__(16) unsigned char smem[];
   // a packed launch that follows this one as its programmatic dependent (a
@@ -447,12 +439,12 @@ cudaError_t launch_one(const PackedLaunch &L, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (CL == 1 && !L.after_packed) {
-    k<<<L.ntets, kPackedLanes, smem, st>>>(L.tets, L.order);
+    k<<<L.ntets, cta_lanes(CL), smem, st>>>(L.tets, L.order);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(L.ntets * CL);
-  cfg.blockDim = dim3(kPackedLanes);
+  cfg.blockDim = dim3(cta_lanes(CL));
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
@@ -546,13 +538,14 @@ __global__ void __launch_bounds__(256) packed_io_kernel(const DevTet *__restrict
 
 }  // namespace
 
-size_t packed_smem_bytes(int reg) {
-  return (size_t)RR * RW * 4 + (size_t)QS * LN * 16 + (size_t)LN * 32 + (size_t)LN * 4 * (reg + 1) * 8;
+size_t packed_smem_bytes(int reg, int cl) {
+  const size_t LN = cta_lanes(cl);
+  return (size_t)RR * ring_row(cl) * 4 + QS * LN * 16 + LN * 32 + LN * 4 * (reg + 1) * 8;
 }
 
 cudaError_t launch_packed(const PackedLaunch &L, cudaStream_t st) {
   if (L.ntets <= 0) return cudaSuccess;
-  const size_t smem = packed_smem_bytes(L.reg);
+  const size_t smem = packed_smem_bytes(L.reg, L.cl);
   switch (L.reg) {  // the packed row tables are padded to degree 3 or 6
     case 3: return launch_dx<3>(L, smem, st);
     case 6: return launch_dx<6>(L, smem, st);

@@ -1,11 +1,13 @@
 // packed.h -- the packed substitution kernels of the FP32 sweeps (packed.cu)
 // and their host-side row schedules (packed_plan.cpp).
 //
-// A packed launch gives every macro-tetrahedron one cluster of c CTAs of
-// kPackedLanes threads each (c = 1 up to level 7, 2 at level 8), which
-// runs the tet's whole forward substitution and then its whole backward
-// substitution (Alg. 2 of arXiv 2210.15280) without waiting on any other
-// cluster.  The interior rows (y, z) are packed onto the cluster's lanes: a
+// A packed launch gives every macro-tetrahedron one CTA of kPackedLanes
+// threads (up to level 7) or one cluster of two CTAs of kPackedClusterLanes
+// threads (level 8), which runs the tet's whole forward substitution and then
+// its whole backward substitution (Alg. 2 of arXiv 2210.15280) without
+// waiting on any other tet.  In a cluster every CTA keeps the whole ring:
+// a lane stores each result into its own CTA's ring and into the other's, so
+// every producer read is a local shared-memory load.  The interior rows (y, z) are packed onto the cluster's lanes: a
 // lane owns one row at a time, keeps that row's surrogate polynomials in
 // registers and computes one point of it per step; the cluster meets at a
 // barrier every q steps (q, the schedule's quantum: 1, 2 or 4 by level).
@@ -31,11 +33,20 @@
 #include <string>
 #include <vector>
 
+#if defined(__CUDACC__)
+#define ILU_PACKED_HD __host__ __device__
+#else
+#define ILU_PACKED_HD
+#endif
+
 namespace ilu {
 
-constexpr int kPackedLanes = 384;  // threads (row lanes) of a packed CTA
-constexpr int kPackedRing = 32;    // steps of each lane's results kept in shared memory
-constexpr int kPackedRingRow = kPackedLanes + 8;  // words per ring row (column kPackedLanes is never written)
+constexpr int kPackedLanes = 384;         // threads (row lanes) of a packed CTA on its own
+constexpr int kPackedClusterLanes = 320;  // threads of each CTA of a two-CTA cluster (the whole ring of
+                                          // both CTAs' lanes fits the shared memory of each)
+constexpr int kPackedRing = 32;           // steps of each lane's results kept in shared memory
+// words per ring row for a schedule of n lanes: column n is never written
+ILU_PACKED_HD constexpr int packed_ring_row(int lanes) { return lanes + 8; }
 constexpr int kPackedQueue = 8;    // input queue slots per lane
 constexpr int kPackedPre = 7;      // input prefetch distance in steps (below the slot count: the
                                    // entry read at a step is never the one being refilled)
@@ -45,7 +56,7 @@ constexpr int kPackedMaxDegree = 6;  // highest row degree (its coefficients fil
 
 // A producer code tells a consumer row where the values of one of its three
 // producer rows are (bits 30-31 the mode): the producer's lane (over the
-// whole cluster) in bits 0-9, the step distance k0 of the first value the
+// whole cluster, at most 1016) in bits 0-9, the step distance k0 of the first value the
 // consumer reads at a step (the second is written one step later) in bits
 // 10-29, and
 //   kProdNone    no such interior row (read from the ring column nothing
@@ -58,15 +69,15 @@ enum { kProdNone = 0, kProdRing = 1, kProdGlobal = 2 };
 inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 10); }
 
 // One row of a schedule (32 bytes), in the pass's own steps:
-//   sw_dlo  sw | (lo - sw) << 16: the switch step sw (q - 1 mod q) and the
-//           step lo of the row's first point (lo - sw in 1..q);
+//   sw_dlo  sw | (lo - sw) << 16 | far << 20: the switch step sw (q - 1 mod
+//           q), the step lo of the row's first point (lo - sw in 1..q), bit
+//           j of far set if producer j comes through the queue;
 //   nyz     n | y << 10 | z << 20 (n = points of the row);
-//   r01g    R0 | R1 << 14 | far << 28, r2rid R2 | row id << 14 | cta << 29:
-//           R_j is the word, in the ring of the CTA holding producer j, of
-//           the value read at the first step of the kPackedBlock-step block
-//           holding sw (kPackedLanes if the producer row does not exist or
-//           comes through the queue), bit j of far set if producer j comes
-//           through the queue, bit j of cta the CTA (cluster rank) of its lane;
+//   r01g    R0 | R1 << 15, r2rid R2 | row id << 15: R_j is the word, in the
+//           ring (rows of packed_ring_row(lanes) words), of the value read
+//           at the first step of the kPackedBlock-step block holding sw
+//           (column `lanes`, which nothing writes, if the producer row does
+//           not exist or comes through the queue);
 //   tt0     the row coordinate t of the point at step sw (float bits);
 //   p[3]    the three producer codes.
 struct PackedEntry {
@@ -74,13 +85,10 @@ struct PackedEntry {
 };
 
 // slot of step s, lane l in the packed array of `lanes` lanes
-#if defined(__CUDACC__)
-__host__ __device__
-#endif
-inline int packed_index32(int s, int l, int lanes) { return (((s >> 2) * lanes + l) << 2) + (s & 3); }
+ILU_PACKED_HD inline int packed_index32(int s, int l, int lanes) { return (((s >> 2) * lanes + l) << 2) + (s & 3); }
 
 struct PackedPlan {
-  int N = 0, lanes = 0, q = 1, nsteps = 0;  // lanes: kPackedLanes per CTA of the cluster; q: the start
+  int N = 0, lanes = 0, q = 1, nsteps = 0;  // lanes: all lanes of the tet's CTA or cluster; q: the start
                                             // quantum; nsteps = T, the steps of either pass (a multiple of
                                             // kPackedBlock)
   std::vector<PackedEntry> fwd, bwd;  // grouped by lane, each lane's rows in step order
@@ -93,13 +101,14 @@ struct PackedPlan {
 // (y-1, z), (y, z-1), (y+1, z-1); the backward ones (y+1, z), (y, z+1),
 // (y-1, z+1).  False (with err) if a check of the schedule fails.
 bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err);
-// The start quantum and the cluster size (CTAs per tet) of the kernels'
-// schedules at N.
+// The start quantum, the cluster size (CTAs per tet) and the lanes of the
+// kernels' schedules at N.
 int packed_quantum(int N);
 int packed_cluster(int N);
-// The plan on packed_cluster(N) x kPackedLanes lanes with the level's
-// quantum, computed once per level and kept for the life of the process;
-// null (with err) if the schedule fails.
+int packed_lanes(int N);
+// The plan on packed_lanes(N) lanes with the level's quantum, computed once
+// per level and kept for the life of the process; null (with err) if the
+// schedule fails.
 const PackedPlan *packed_plan_cached(int N, std::string *err);
 
 }  // namespace ilu

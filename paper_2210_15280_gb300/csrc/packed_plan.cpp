@@ -58,9 +58,11 @@ namespace ilu {
 
 int packed_quantum(int N) { return N <= 64 ? 1 : (N <= 128 ? 2 : 4); }
 int packed_cluster(int N) { return N <= 128 ? 1 : 2; }
+int packed_lanes(int N) { return packed_cluster(N) == 1 ? kPackedLanes : 2 * kPackedClusterLanes; }
 
 bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err) {
-  if (N < 4 || N > 256 || lanes < 1 || lanes > 1023 || (q != 1 && q != 2 && q != 4)) {
+  // lanes <= 1016: every ring word (below 32 rows of lanes + 8 words) fits 15 bits
+  if (N < 4 || N > 256 || lanes < 1 || lanes > 1016 || (q != 1 && q != 2 && q != 4)) {
     *err = "packed schedule: bad size";
     return false;
   }
@@ -153,6 +155,7 @@ bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err
   // q - 1 steps apart: a value read from the ring must not be overwritten by
   // then (k0 <= kPackedRing + 1 - q)
   const int ring_max = std::min(kPackedRing - 1, kPackedRing + 1 - q);
+  const int RW = packed_ring_row(lanes);
   for (int l = 0; l < lanes; ++l) {
     out->lane_off[l] = (int)out->fwd.size();
     const std::vector<int> &ids = per_lane[l];
@@ -164,14 +167,13 @@ bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err
         const int lo = first(id, fwd);
         const int sw = fwd ? s_of[id] - 1 : T - s_of[id] - np - 1;  // a multiple of q, minus 1
         const int tau0 = sw & ~(kPackedBlock - 1);
-        int code[3], R3[3], gm = 0, cta = 0;
+        int code[3], R3[3], gm = 0;
         for (int j = 0; j < 3; ++j) {
           // producers: forward (y-1, z), (y, z-1), (y+1, z-1); backward (y+1, z), (y, z+1), (y-1, z+1)
           const int64_t p = fwd ? rid(y + pdy[j], z + pdz[j]) : rid(y - pdy[j], z - pdz[j]);
           if (p < 0) {
             code[j] = prod_code(kProdNone, 0, 0);
-            R3[j] = kPackedLanes;  // the ring column nothing writes, in the consumer's own CTA
-            cta |= lane_of[id] / kPackedLanes << j;
+            R3[j] = lanes;  // the ring column nothing writes
             continue;
           }
           const int k0 = lo - first(p, fwd) + (fwd ? pc[j] : 1);
@@ -187,19 +189,16 @@ bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err
             return false;
           }
           code[j] = prod_code(ring ? kProdRing : kProdGlobal, lane_of[p], k0);
-          R3[j] = ring ? ((tau0 + 1 - k0) & (kPackedRing - 1)) * kPackedRingRow + lane_of[p] % kPackedLanes
-                       : kPackedLanes;
+          R3[j] = ring ? ((tau0 + 1 - k0) & (kPackedRing - 1)) * RW + lane_of[p] : lanes;
           gm |= ring ? 0 : 1 << j;
-          // a queue producer reads the consumer's own zero column
-          cta |= (ring ? lane_of[p] : lane_of[id]) / kPackedLanes << j;
         }
         const int K = N - y - z, xsw = fwd ? 0 : n + lo - sw;
         const float tt0 = (float)((double)(2 * xsw - K) * hh);
         PackedEntry e;
-        e.sw_dlo = sw | ((lo - sw) << 16);
+        e.sw_dlo = sw | ((lo - sw) << 16) | (gm << 20);
         e.nyz = n | (y << 10) | (z << 20);
-        e.r01g = R3[0] | (R3[1] << 14) | (gm << 28);
-        e.r2rid = R3[2] | (id << 14) | (cta << 29);
+        e.r01g = R3[0] | (R3[1] << 15);
+        e.r2rid = R3[2] | (id << 15);
         std::memcpy(&e.tt0, &tt0, sizeof(float));
         for (int j = 0; j < 3; ++j) e.p[j] = code[j];
         (fwd ? out->fwd : out->bwd).push_back(e);
@@ -222,7 +221,7 @@ const PackedPlan *packed_plan_cached(int N, std::string *err) {
   auto &slot = cache[N];
   if (!slot) {
     auto p = std::make_unique<PackedPlan>();
-    if (!make_packed_plan(N, packed_cluster(N) * kPackedLanes, packed_quantum(N), p.get(), err)) return nullptr;
+    if (!make_packed_plan(N, packed_lanes(N), packed_quantum(N), p.get(), err)) return nullptr;
     slot = std::move(p);
   }
   return slot.get();

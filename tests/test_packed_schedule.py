@@ -19,7 +19,7 @@ import pytest
 
 import seeded_inputs as si
 
-RING, SLOTS, PRE, LANES, RW, BLOCK = 32, 8, 7, 384, 392, 8
+RING, SLOTS, PRE, LANES, CLUSTER_LANES, BLOCK = 32, 8, 7, 384, 2 * 320, 8
 
 
 @pytest.fixture(scope="module")
@@ -33,12 +33,13 @@ def decode(e):
     """(switch step, first point step, n, y, z, producer codes, ring words,
     far bits, row id, t at the switch step) of a schedule entry"""
     w = [int(v) & 0xffffffff for v in e]
-    sw, lo = w[0] & 0xffff, (w[0] & 0xffff) + (w[0] >> 16)
+    sw, lo = w[0] & 0xffff, (w[0] & 0xffff) + ((w[0] >> 16) & 15)
+    gm = (w[0] >> 20) & 7
     n, y, z = w[1] & 1023, (w[1] >> 10) & 1023, w[1] >> 20
-    R = [w[2] & 0x3fff, (w[2] >> 14) & 0x3fff, w[3] & 0x3fff]
-    gm, rid, cta = (w[2] >> 28) & 7, (w[3] >> 14) & 0x7fff, w[3] >> 29
+    R = [w[2] & 0x7fff, (w[2] >> 15) & 0x7fff, w[3] & 0x7fff]
+    rid = (w[3] >> 15) & 0x7fff
     tt0 = float(np.array([w[4]], dtype=np.uint32).view(np.float32)[0])
-    return dict(sw=sw, lo=lo, n=n, y=y, z=z, codes=w[5:8], R=R, gm=gm, rid=rid, cta=cta, tt0=tt0)
+    return dict(sw=sw, lo=lo, n=n, y=y, z=z, codes=w[5:8], R=R, gm=gm, rid=rid, tt0=tt0)
 
 
 def lane_k0(c):
@@ -55,7 +56,7 @@ def quantum_of(level):
 
 
 def lanes_of(level):
-    return LANES if level <= 7 else 2 * LANES
+    return LANES if level <= 7 else CLUSTER_LANES
 
 
 def emulate_pass(N, T, lanes, rows, forward, Ls, Dinv, point_id, pw, B=1):
@@ -262,6 +263,7 @@ def test_schedule_covers_every_row_once(g, orc, level):
     _, _, eb, _ = g.packed_schedule(level, False)
     assert T % BLOCK == 0 and ln == lanes_of(level)
     ring_max = min(RING - 1, RING + 1 - q)
+    RW = ln + 8  # ring row: every lane's column, then column ln that nothing writes
     for fwd, ent in ((True, ef), (False, eb)):
         rows = [decode(e) for e in ent]
         assert len({(r["y"], r["z"]) for r in rows}) == len(rows) == (N - 3) * (N - 2) // 2
@@ -277,18 +279,14 @@ def test_schedule_covers_every_row_once(g, orc, level):
                 lane_p, k0 = lane_k0(c)
                 if md == 1:
                     assert q + 1 <= k0 <= ring_max
-                    assert r["R"][j] == ((tau0 + 1 - k0) % RING) * RW + lane_p % LANES
-                    assert ((r["cta"] >> j) & 1) == lane_p // LANES  # the ring of the producer's CTA
+                    assert r["R"][j] == ((tau0 + 1 - k0) % RING) * RW + lane_p
                 else:
-                    assert r["R"][j] == LANES and (k0 > ring_max if md == 2 else k0 == 0)
+                    assert r["R"][j] == ln and (k0 > ring_max if md == 2 else k0 == 0)
                 assert ((r["gm"] >> j) & 1) == (md == 2)
         for l in range(ln):
             prev = None
             for e in ent[off[l]:off[l + 1]]:
                 r = decode(e)
-                for j, c in enumerate(r["codes"]):
-                    if mode(c) != 1:  # no ring producer: the consumer's own CTA (its zero column)
-                        assert ((r["cta"] >> j) & 1) == l // LANES
                 if prev is not None:
                     assert r["sw"] >= prev["lo"] + prev["n"]          # the step after a row has no point
                     assert r["sw"] >= prev["sw"] + PRE + 1            # the stage is free for the copy

@@ -348,7 +348,7 @@ def batch_workload(args, g, torch, rank=0, world=1, dist=None, compact=False):
                             "packed kernels, one graph replay per sweep",
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "kernel": "whole sweep at 24 B/DoF", "peak_source": src},
-                "depth": {"note": "the level-8 tets' packed substitutions bound the batch (one SM each)"},
+                "depth": {"note": "the level-8 tets' packed substitutions bound the batch (two SMs each)"},
                 "one_by_one": per_tet,
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": nbytes}}
     return {"metric": f"smoother DoF-sweeps/s (batch of {n} macro-tets, FP32 sweeps)", "value": value, "unit": UNIT,

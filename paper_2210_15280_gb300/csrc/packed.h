@@ -69,19 +69,19 @@ enum { kProdNone = 0, kProdRing = 1, kProdGlobal = 2 };
 inline int prod_code(int mode, int slot, int k0) { return (mode << 30) | slot | (k0 << 10); }
 
 // One row of a schedule (32 bytes), in the pass's own steps:
-//   sw_dlo  sw | (lo - sw) << 16 | far << 20: the switch step sw (q - 1 mod
-//           q), the step lo of the row's first point (lo - sw in 1..q), bit
-//           j of far set if producer j comes through the queue;
-//   nyz     n | y << 10 | z << 20 (n = points of the row);
-//   r01g    R0 | R1 << 15, r2rid R2 | row id << 15: R_j is the word, in the
-//           ring (rows of packed_ring_row(lanes) words), of the value read
-//           at the first step of the kPackedBlock-step block holding sw
-//           (column `lanes`, which nothing writes, if the producer row does
-//           not exist or comes through the queue);
-//   tt0     the row coordinate t of the point at step sw (float bits);
-//   p[3]    the three producer codes.
+//   sw_dlo_far  sw | (lo - sw) << 16 | far << 20: the switch step sw (q - 1
+//               mod q), the step lo of the row's first point (lo - sw in
+//               1..q), bit j of far set if producer j comes through the queue;
+//   nyz         n | y << 10 | z << 20 (n = points of the row);
+//   r01, r2rid  R0 | R1 << 15 and R2 | row id << 15: R_j is the word, in
+//               the ring (rows of packed_ring_row(lanes) words), of the value
+//               read at the first step of the kPackedBlock-step block holding
+//               sw (column `lanes`, which nothing writes, if the producer row
+//               does not exist or comes through the queue);
+//   tt0         the row coordinate t of the point at step sw (float bits);
+//   p[3]        the three producer codes.
 struct PackedEntry {
-  int sw_dlo, nyz, r01g, r2rid, tt0, p[3];
+  int sw_dlo_far, nyz, r01, r2rid, tt0, p[3];
 };
 
 // slot of step s, lane l in the packed array of `lanes` lanes

@@ -195,9 +195,9 @@ bool make_packed_plan(int N, int lanes, int q, PackedPlan *out, std::string *err
         const int K = N - y - z, xsw = fwd ? 0 : n + lo - sw;
         const float tt0 = (float)((double)(2 * xsw - K) * hh);
         PackedEntry e;
-        e.sw_dlo = sw | ((lo - sw) << 16) | (gm << 20);
+        e.sw_dlo_far = sw | ((lo - sw) << 16) | (gm << 20);
         e.nyz = n | (y << 10) | (z << 20);
-        e.r01g = R3[0] | (R3[1] << 15);
+        e.r01 = R3[0] | (R3[1] << 15);
         e.r2rid = R3[2] | (id << 15);
         std::memcpy(&e.tt0, &tt0, sizeof(float));
         for (int j = 0; j < 3; ++j) e.p[j] = code[j];

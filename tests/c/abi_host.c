@@ -69,6 +69,20 @@ int main(void) {
   CHECK(ilu_setup(P, 4, &k, 3, &o, &t) == ILU_OK && t != NULL, "tabulated values accepted for F64");
   ilu_destroy(t);
   t = NULL;
+  /* batch calls refuse null arguments without touching a device */
+  {
+    int per_sweep = -1;
+    CHECK(ilu_batch_launches(NULL, &per_sweep) == ILU_EINVAL && per_sweep == -1, "batch_launches(NULL batch)");
+    CHECK(ilu_batch_create(NULL, 0, NULL, NULL) == ILU_EINVAL, "batch_create(NULL)");
+  }
+  /* the packed row schedule (host code): the level-8 plan runs on 640 lanes */
+  {
+    int nsteps = 0, lanes = 0;
+    CHECK(ilu_packed_schedule(8, 1, 0, 0, &nsteps, &lanes, NULL, NULL) == ILU_OK && lanes == 640 &&
+              nsteps % 8 == 0 && nsteps > 0,
+          "level-8 packed schedule on 640 lanes");
+    CHECK(ilu_packed_schedule(8, 1, 1017, 0, &nsteps, &lanes, NULL, NULL) == ILU_EINVAL, "more than 1016 lanes");
+  }
   CHECK(strlen(ilu_version()) > 0, "version");
   return fails ? 1 : 0;
 }

@@ -123,19 +123,21 @@ __device__ __forceinline__ void pass_sync() {
 // (coefficients from the stage, the entry after it from `sent`).  Switch
 // steps are Q - 1 (mod Q), so only those unrolled positions test for events.
 //
-// The CTA meets at a block barrier after every step Q - 1 (mod Q): the
+// The CTA (cluster) meets at a barrier after every step Q - 1 (mod Q): the
 // schedule keeps every producer value at least Q + 1 steps ahead of the step
 // that reads it and reads the ring only up to kPackedRing + 1 - Q steps back,
 // so a value is visible when read and not yet overwritten, however far apart
-// the lanes are between two barriers.  A lane's own stage and `sent` are
+// the lanes are between two barriers.  In a cluster each CTA holds the ring
+// of all lanes: a lane writes its result into its own CTA's ring and the
+// other's, and the barrier's release and acquire order both.  A lane's own stage and `sent` are
 // refilled only after the barrier that follows the switch step reading them.
 //
 // Steps with no point of the lane write 0.  The schedule leaves such a step
 // before and after every row, in both passes, and these are exactly the
 // steps at which a consumer reads a producer's missing neighbour (x = 0, or
 // one past the producer row's end); a producer row that does not exist is
-// read from ring column kPackedLanes, which is never written.  So the point
-// arithmetic needs no masks.
+// read from ring column LT (after every lane's column), which is never
+// written.  So the point arithmetic needs no masks.
 //
 // The loop runs in blocks of kPackedBlock steps, unrolled, so that ring rows
 // and queue slots are compile-time offsets from per-block bases: ring row
